@@ -56,6 +56,31 @@ def test_voxel_single_voxel_closed_form_3d():
     np.testing.assert_allclose(w, [amp / 4] * 4, rtol=1e-14)
 
 
+@pytest.mark.parametrize("det", ["flat", "curved"])
+def test_voxel_off_axis_closed_form_3d(det):
+    """Off-axis voxel at (40, 0, 30) under theta = 0, SAD 500, SDD 1000, so
+    w = (40, -500, 30), r = sqrt(252500).  Flat: depth = w.n = 500, amplitude
+    V r SDD^2 / (depth^3 du dv).  Curved: rho = sqrt(40^2 + 500^2), amplitude
+    V r SDD^2 / (rho^3 du dv).  (Point mass over the ray density there.)"""
+    spec = W.GeometrySpec("circ3d", det, 3, 1, 3, 40.0, 10.0, 30.0, 128, 96, 2.0, 2.0, 1,
+                          theta=0.0, sad=500.0, sdd=1000.0)
+    _, _, w = oracle.footprint(spec, "voxel", 0, 2, 0, 2)
+    r = math.sqrt(252500.0)
+    rho = 500.0 if det == "flat" else math.sqrt(40.0 ** 2 + 500.0 ** 2)
+    want = 40.0 * 10.0 * 30.0 * r * 1e6 / (rho ** 3 * 4.0)
+    assert w.sum() == pytest.approx(want, rel=1e-13)
+
+
+def test_voxel_off_axis_closed_form_2d():
+    """2D: pixel at (40, 0): r = sqrt(40^2 + 500^2), depth 500, amplitude
+    dx dy r SDD / (depth^2 du)."""
+    spec = W.GeometrySpec("fan2d", "flat", 3, 1, 1, 40.0, 10.0, 1.0, 128, 1, 2.0, 1.0, 1,
+                          theta=0.0, sad=500.0, sdd=1000.0)
+    _, _, w = oracle.footprint(spec, "voxel", 0, 2, 0, 0)
+    want = 40.0 * 10.0 * math.sqrt(40.0 ** 2 + 500.0 ** 2) * 1000.0 / (500.0 ** 2 * 2.0)
+    assert w.sum() == pytest.approx(want, rel=1e-13)
+
+
 def test_voxel_curved_amplitude_closed_form():
     """Curved 2D: amplitude dx dy SDD / (rho du) where rho is the voxel's
     distance from the source; a voxel at (0, 0) under theta = 0 has rho = SAD."""
