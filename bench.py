@@ -1,0 +1,292 @@
+#!/usr/bin/env python
+"""Throughput of the separable-footprint (SF-TR) cone-beam projector pair.
+
+One step = SF forward projection y = A x followed by SF backprojection
+A^T y over the 3D circular cone-beam workload: 256^3 volume of 0.5 mm voxels,
+360 views over 360 deg, flat 512 x 384 detector of 0.8 mm, SAD 785 / SDD 1085
+mm, seeded random-ellipsoid phantom (values 0-0.03 / mm).  Metric: giga voxel
+updates per second, an update being one (voxel, view) pair, two per pair per
+step (forward and back).  Per-step working set (67 MB volume + 283 MB
+sinogram) exceeds the 129 MB L2.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 (under torchrun): every rank runs its own replica of the workload
+(independent problems, no collective on the data path); value = all ranks'
+updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SF cone-beam fwd+back GUpdates/s & %HBM roofline; served p50/p99 latency"
+UNIT = "GUpdates/s"
+WORKLOAD = ("3D circular cone-beam SF-TR forward+back, 256^3 x 0.5 mm FP32 volume, 360 views, "
+            "flat 512x384 detector 0.8 mm, SAD 785 / SDD 1085 mm")
+# FP32 operations per (voxel, view) update of the SF-TR weight evaluation and
+# accumulation in circular geometry (derivation in the design notes).
+SF_FLOPS_PER_UPDATE = 30.0
+N_SM, FP32_LANES = 152, 128
+
+# DRAM bytes per launch from one ncu capture of the same kernel source
+# (sha256 of the .cu at capture time); null once the source changes.
+NCU_TRAFFIC = {}
+
+
+def _src_hash(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2503_16741_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [l.split(",") for l in self.lines if l.count(",") >= 8]
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(spec, nviews: int, x=None):
+    """The FP64 oracle timed on the host cores on a view-decimated copy of
+    the workload (nviews evenly spaced views): SF forward + SF back."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    oracle.build()
+    views = np.round(np.arange(nviews) * spec.nview / nviews).astype(int)
+    sub = spec.subset(views)
+    if x is None:
+        x = W.phantom(spec, seed=0)
+    t0 = time.perf_counter()
+    y = oracle.forward(sub, "sf", x)
+    oracle.back(sub, "sf", y)
+    dt = time.perf_counter() - t0
+    upd = 2.0 * spec.n_vox * nviews
+    return upd / dt / 1e9, dt, oracle.max_threads(), f"{nviews} of {spec.nview} views, full volume"
+
+
+def run_reference(args):
+    """The oracle as the reference arm: K timed steps of a bounded sample."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import workloads as W
+    spec = W.circ3d_256()
+    x = W.phantom(spec, seed=0)
+    nviews = args.ref_views
+    for _ in range(args.warmup):
+        cpu_oracle_sample(spec, nviews, x)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dt, cores, sample = cpu_oracle_sample(spec, nviews, x)
+        t += dt
+    upd = 2.0 * spec.n_vox * nviews * args.steps
+    val = upd / t / 1e9
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD + f" (oracle sample: {sample})"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-views", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2503_16741_gb300 as ct
+    import workloads as W
+    from paper_2503_16741_gb300 import build as cbuild
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cbuild.build()
+    dev = torch.device("cuda", local)
+    spec = W.circ3d_256()
+    geom = ct.Geometry.from_spec(spec)
+    x = W.phantom(spec, seed=0, device=dev, dtype=torch.float32)
+    y = torch.empty(spec.sino_shape, dtype=torch.float32, device=dev)
+    xb = torch.empty(spec.vol_shape, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ct.forward_into(geom, x, y, "sf", stream=stream)
+        ct.back_into(geom, y, xb, "sf", stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    for k in range(K):
+        ev[k][0].record(stream)
+        ct.forward_into(geom, x, y, "sf", stream=stream)
+        ev[k][1].record(stream)
+        ct.back_into(geom, y, xb, "sf", stream=stream)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    fwd_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
+    back_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    total_ms = ev[0][0].elapsed_time(ev[-1][2])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+    upd_step = 2.0 * spec.n_vox * spec.nview
+    value = upd_step * K * ws / (total_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (pinned)
+    xh = x.cpu().pin_memory()
+    xbh = torch.empty(spec.vol_shape, dtype=torch.float32).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        step()
+        xbh.copy_(xb, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        xd.copy_(xh, non_blocking=True)
+        ct.forward_into(geom, xd, y, "sf", stream=stream)
+        ct.back_into(geom, y, xb, "sf", stream=stream)
+        xbh.copy_(xb, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / K
+    e2e = {"value": upd_step / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": xh.numel() * 4, "d2h_bytes_per_step": xbh.numel() * 4}
+
+    if rank != 0:
+        return
+    peaks = _peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    dom, dom_ms, dom_src = ("sf_back", back_ms, "k_sf.cu") if back_ms >= fwd_ms else \
+        ("sf_fwd", fwd_ms, "k_sf.cu")
+    flops = SF_FLOPS_PER_UPDATE * spec.n_vox * spec.nview
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(dom_src) else None
+    vol_b, sino_b = spec.n_vox * 4, spec.n_cells * 4
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_ach = (vol_b + sino_b) / (dom_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "projector": "SF-TR", "batch": 1,
+                   "l2": "inputs larger than L2 (67 MB volume + 283 MB sinogram per step)",
+                   "fwd_ms": fwd_ms, "back_ms": back_ms},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic,
+                     "peak_note": f"FP32 FMA peak {N_SM} SM x {FP32_LANES} lanes x 2 at {sm_mhz:.0f} MHz",
+                     "flops_per_update": SF_FLOPS_PER_UPDATE},
+        "hbm_roofline": {"kernel": dom, "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_ach / hbm_peak, "bytes": "compulsory: read input once, write output once",
+                         "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": e2e,
+        "gpu_launches": 2 * K,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        val, dt, cores, sample = cpu_oracle_sample(spec, 8)
+        out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample + f" ({dt:.1f} s)"}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * ctproj.h -- C ABI of the GB300 CT projector library (libctproj.so).
+ *
+ * The library computes the forward projection y = A x and its adjoint
+ * backprojection x = A^T y of CTorch (arXiv 2503.16741, Sec. 2.3, Eq. 1 and
+ * Eq. 2) for the scan geometries of Sec. 2.2 (2D fan beam, 3D circular and
+ * non-circular cone beam, flat or curved detector, per-view parameters) and
+ * the four projector algorithms of Sec. 2.3 (voxel-driven, ray-driven,
+ * distance-driven, separable footprint).  The system matrix A is never
+ * stored; every call recomputes its weights on the GPU (Sec. 2.3).
+ *
+ * Data layout (Sec. 1, "batched and channeled" PyTorch tensors):
+ *   volume   [batch][nz][ny][nx], x fastest   (2D: nz = 1)
+ *   sinogram [batch][nview][nv][nu], u fastest (2D: nv = 1)
+ * where batch = B * C of the PyTorch tensor.  Buffers are contiguous device
+ * memory owned by the caller.
+ *
+ * Threading: every call is asynchronous on the CUDA stream it is given and
+ * performs no host-device synchronisation and no allocation, except
+ * ct_geometry_create / ct_geometry_destroy, which allocate and free the
+ * device copy of the per-view geometry table on the current device.
+ * Results are deterministic: no atomics, fixed summation order.
+ *
+ * Errors: each call returns a ct_status; ct_last_error() gives a message for
+ * the last non-OK status returned on the calling thread.
+ */
+#ifndef CTPROJ_H
+#define CTPROJ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Scan geometry kinds (Sec. 2.2, Table 1). */
+typedef enum {
+    CT_FAN2D = 0,      /* 2D fan beam: theta, SAD, SDD, x_src, x/y_ofst, u_ofst      */
+    CT_CIRC3D = 1,     /* 3D circular cone beam: adds z_src, z_ofst, v_ofst          */
+    CT_NONCIRC3D = 2   /* 3D non-circular: adds phi (about x) and psi (about y)      */
+} ct_geom_kind;
+
+/* Detector models (Sec. 2.2): flat panel, or a cylindrical arc centred on the
+   source (curved detectors exist for CT_FAN2D and CT_CIRC3D only, Sec. 2.3). */
+typedef enum { CT_DET_FLAT = 0, CT_DET_CURVED = 1 } ct_det_kind;
+
+/* Projector algorithms (Sec. 2.3). */
+typedef enum {
+    CT_VOXEL = 0,  /* voxel-driven: point voxel, bilinear detector interpolation (Peters 1981) */
+    CT_RAY = 1,    /* ray-driven: exact chord lengths of the cell-centre ray (Siddon 1985)     */
+    CT_DD = 2,     /* distance-driven: boundary overlaps (De Man & Basu 2004)                 */
+    CT_SF = 3      /* separable footprint SF-TR: trapezoid x rectangle (Long et al. 2010)     */
+} ct_projector;
+
+/* Projection modes (Sec. 2.3): "proj" is the matched pair; "recon" (FBP
+   depth weighting) is not provided and returns CT_ERR_UNSUPPORTED. */
+typedef enum { CT_MODE_PROJ = 0, CT_MODE_RECON = 1 } ct_mode;
+
+/* Storage types of volume and sinogram.  Arithmetic is FP32 in all cases;
+   half types are converted on load and rounded once on store. */
+typedef enum { CT_F32 = 0, CT_F16 = 1, CT_BF16 = 2 } ct_dtype;
+
+typedef enum {
+    CT_OK = 0,
+    CT_ERR_INVALID_ARG = 1,   /* bad size, pointer, vector length or geometry          */
+    CT_ERR_UNSUPPORTED = 2,   /* valid request outside what the library implements     */
+    CT_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed           */
+    CT_ERR_OOM = 4,           /* device allocation failed                              */
+    CT_ERR_TIMEOUT = 5        /* reserved for host-side watchdogs of callers           */
+} ct_status;
+
+/* Geometry description (Sec. 2.2 and Table 1).  Lengths in mm, angles in
+ * radians.  Each per-view parameter is an array of length n_<name>, which
+ * must be 1 (shared by all views) or nview (one value per view); a NULL
+ * pointer means 0.0 for every view.  sad and sdd must be given.
+ *
+ * World frame: origin at the rotation centre; at theta = 0 the y axis is
+ * normal to the detector, the source is at (x_src, SAD, z_src) and the
+ * detector centre at (-u_ofst, SAD - SDD, -v_ofst), with detector axes
+ * e_u = (1,0,0) and e_v = (0,0,1).  The gantry rotation R = Rz(theta)
+ * Rx(phi) Ry(psi) (rotation order y, then x, then z) moves source and
+ * detector; the object stays fixed.  Voxel (i,j,k) is centred at
+ * ((i-(nx-1)/2) dx + x_ofst, (j-(ny-1)/2) dy + y_ofst, (k-(nz-1)/2) dz + z_ofst).
+ * Detector cell (a,b) is centred at u = (a-(nu-1)/2) du, v = (b-(nv-1)/2) dv
+ * from the detector centre along e_u, e_v; on a curved detector u is the arc
+ * length on the cylinder of radius SDD around the axis through the source
+ * along e_v.  For CT_FAN2D, nz and nv must be 1 and dz, dv, z_src, z_ofst,
+ * v_ofst, phi, psi are ignored.
+ *
+ * poses (optional, CT_NONCIRC3D only): nview x 12 doubles per view
+ * (source xyz, detector-centre xyz, e_u xyz, e_v xyz) replacing the angle
+ * parametrisation; e_u and e_v must be orthonormal.  The object offsets still
+ * apply.  The volume must lie in front of the source and behind nothing: for
+ * every view each volume corner must be between the source and the detector
+ * plane (flat) or cylinder (curved), else CT_ERR_INVALID_ARG. */
+typedef struct {
+    int kind;                  /* ct_geom_kind */
+    int det;                   /* ct_det_kind  */
+    int nx, ny, nz;
+    double dx, dy, dz;
+    int nu, nv;
+    double du, dv;             /* du is an arc length on a curved detector */
+    int nview;
+    const double *theta, *phi, *psi;            int n_theta, n_phi, n_psi;
+    const double *sad, *sdd;                    int n_sad, n_sdd;
+    const double *x_src, *z_src;                int n_x_src, n_z_src;
+    const double *x_ofst, *y_ofst, *z_ofst;     int n_x_ofst, n_y_ofst, n_z_ofst;
+    const double *u_ofst, *v_ofst;              int n_u_ofst, n_v_ofst;
+    const double *poses;
+} ct_geometry_desc;
+
+typedef struct ct_geometry ct_geometry;
+
+/* Validate the description, compute the per-view tables in FP64 (source,
+ * detector frame, voxel-index-to-detector maps, footprint search margins),
+ * round them once to FP32 and upload them to the current CUDA device.
+ * The description's arrays are copied; the caller may free them afterwards.
+ * On success *out owns the tables until ct_geometry_destroy.
+ * Returns CT_ERR_INVALID_ARG for a malformed description,
+ * CT_ERR_UNSUPPORTED for a curved non-circular geometry (Sec. 2.3),
+ * CT_ERR_OOM / CT_ERR_CUDA for device failures. */
+ct_status ct_geometry_create(const ct_geometry_desc *desc, ct_geometry **out);
+
+/* Free the device table and the host copy.  NULL is accepted. */
+ct_status ct_geometry_destroy(ct_geometry *geom);
+
+/* Sizes of the geometry: nx, ny, nz, nu, nv, nview (any pointer may be NULL). */
+ct_status ct_geometry_shape(const ct_geometry *geom, int *nx, int *ny, int *nz,
+                            int *nu, int *nv, int *nview);
+
+/* Forward projection y = A x (Sec. 2.3, Eq. 1).
+ * vol:  device pointer, batch x nz x ny x nx elements of type in_t.
+ * sino: device pointer, batch x nview x nv x nu elements of type out_t;
+ *       overwritten (not accumulated).
+ * batch: number of independent volumes (B*C), >= 1.
+ * cuda_stream: cudaStream_t to launch on (NULL = the default stream).
+ * The projector's weights follow the cited method of Sec. 2.3; the same
+ * weight functions serve ct_back, so the pair is matched to FP32 rounding.
+ * CT_SF needs dx == dy.  Inputs and outputs must not overlap.
+ * Must be called with the geometry's device current. */
+ct_status ct_forward(const ct_geometry *geom, ct_projector proj, ct_mode mode,
+                     ct_dtype in_t, const void *vol, ct_dtype out_t, void *sino,
+                     int batch, void *cuda_stream);
+
+/* Backprojection x = A^T y, the exact adjoint of ct_forward (Sec. 2.3, Eq. 2).
+ * sino: device pointer, batch x nview x nv x nu elements of type in_t.
+ * vol:  device pointer, batch x nz x ny x nx elements of type out_t;
+ *       overwritten.  Other arguments as for ct_forward. */
+ct_status ct_back(const ct_geometry *geom, ct_projector proj, ct_mode mode,
+                  ct_dtype in_t, const void *sino, ct_dtype out_t, void *vol,
+                  int batch, void *cuda_stream);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char *ct_last_error(void);
+
+/* Library version string. */
+const char *ct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTPROJ_H */

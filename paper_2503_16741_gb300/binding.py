@@ -1,0 +1,239 @@
+"""ctypes binding of libctproj (include/ctproj.h).
+
+Argument marshalling only: shapes, dtypes and pointers are checked here and
+every projection runs in the library's CUDA kernels.  The library must have
+been built (`paper_2503_16741_gb300.build.build()`); without it every call
+raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+CT_OK = 0
+STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_UNSUPPORTED", 3: "CT_ERR_CUDA",
+          4: "CT_ERR_OOM", 5: "CT_ERR_TIMEOUT"}
+KINDS = {"fan2d": 0, "circ3d": 1, "noncirc3d": 2}
+DETS = {"flat": 0, "curved": 1}
+PROJECTORS = {"voxel": 0, "ray": 1, "dd": 2, "sf": 3}
+MODES = {"proj": 0, "recon": 1}
+DTYPES = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}
+PER_VIEW = ("theta", "phi", "psi", "sad", "sdd", "x_src", "z_src",
+            "x_ofst", "y_ofst", "z_ofst", "u_ofst", "v_ofst")
+
+
+class CTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("det", C.c_int),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("nu", C.c_int), ("nv", C.c_int),
+                ("du", C.c_double), ("dv", C.c_double),
+                ("nview", C.c_int),
+                ("theta", C.POINTER(C.c_double)), ("phi", C.POINTER(C.c_double)),
+                ("psi", C.POINTER(C.c_double)),
+                ("n_theta", C.c_int), ("n_phi", C.c_int), ("n_psi", C.c_int),
+                ("sad", C.POINTER(C.c_double)), ("sdd", C.POINTER(C.c_double)),
+                ("n_sad", C.c_int), ("n_sdd", C.c_int),
+                ("x_src", C.POINTER(C.c_double)), ("z_src", C.POINTER(C.c_double)),
+                ("n_x_src", C.c_int), ("n_z_src", C.c_int),
+                ("x_ofst", C.POINTER(C.c_double)), ("y_ofst", C.POINTER(C.c_double)),
+                ("z_ofst", C.POINTER(C.c_double)),
+                ("n_x_ofst", C.c_int), ("n_y_ofst", C.c_int), ("n_z_ofst", C.c_int),
+                ("u_ofst", C.POINTER(C.c_double)), ("v_ofst", C.POINTER(C.c_double)),
+                ("n_u_ofst", C.c_int), ("n_v_ofst", C.c_int),
+                ("poses", C.POINTER(C.c_double))]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libctproj.so (built in-tree); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2503_16741_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        lib = C.CDLL(path)
+        P = C.POINTER
+        lib.ct_geometry_create.argtypes = [P(_Desc), P(C.c_void_p)]
+        lib.ct_geometry_destroy.argtypes = [C.c_void_p]
+        lib.ct_geometry_shape.argtypes = [C.c_void_p] + [P(C.c_int)] * 6
+        sig = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
+        lib.ct_forward.argtypes = sig
+        lib.ct_back.argtypes = sig
+        lib.ct_last_error.restype = C.c_char_p
+        lib.ct_version.restype = C.c_char_p
+        for f in ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_shape", "ct_forward", "ct_back"):
+            getattr(lib, f).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != CT_OK:
+        raise CTError(rc, load().ct_last_error().decode())
+
+
+class Geometry:
+    """A scan geometry (Sec. 2.2, Table 1) uploaded to the current CUDA device.
+
+    Keyword arguments follow the paper's parameter names; per-view parameters
+    are scalars or length-nview sequences.  `Geometry.from_spec(obj)` reads the
+    same attributes from any object that has them."""
+
+    def __init__(self, kind: str, det: str, nx: int, ny: int, nz: int, dx: float, dy: float,
+                 dz: float, nu: int, nv: int, du: float, dv: float, nview: int,
+                 poses: Optional[np.ndarray] = None, **params):
+        lib = load()
+        unknown = set(params) - set(PER_VIEW)
+        if unknown:
+            raise TypeError(f"unknown geometry parameters {sorted(unknown)}")
+        self.kind, self.det = kind, det
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.nu, self.nv, self.nview = int(nu), int(nv), int(nview)
+        self.dx, self.dy, self.dz, self.du, self.dv = map(float, (dx, dy, dz, du, dv))
+        d = _Desc()
+        d.kind, d.det = KINDS[kind], DETS[det]
+        d.nx, d.ny, d.nz = self.nx, self.ny, self.nz
+        d.dx, d.dy, d.dz = self.dx, self.dy, self.dz
+        d.nu, d.nv, d.du, d.dv, d.nview = self.nu, self.nv, self.du, self.dv, self.nview
+        self._keep = []
+        for name in PER_VIEW:
+            val = params.get(name, 500.0 if name == "sad" else (1000.0 if name == "sdd" else 0.0))
+            arr = np.ascontiguousarray(np.atleast_1d(np.asarray(val, dtype=np.float64)).ravel())
+            self._keep.append(arr)
+            setattr(d, name, arr.ctypes.data_as(C.POINTER(C.c_double)))
+            setattr(d, "n_" + name, int(arr.size))
+        if poses is not None:
+            p = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(self.nview, 12))
+            self._keep.append(p)
+            d.poses = p.ctypes.data_as(C.POINTER(C.c_double))
+        else:
+            d.poses = C.POINTER(C.c_double)()
+        h = C.c_void_p()
+        _check(lib.ct_geometry_create(C.byref(d), C.byref(h)))
+        self._h = h
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def from_spec(cls, spec) -> "Geometry":
+        kw = {n: getattr(spec, n) for n in PER_VIEW}
+        return cls(spec.kind, spec.det, spec.nx, spec.ny, spec.nz, spec.dx, spec.dy, spec.dz,
+                   spec.nu, spec.nv, spec.du, spec.dv, spec.nview,
+                   poses=getattr(spec, "poses", None), **kw)
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise RuntimeError("geometry was closed")
+        return self._h
+
+    @property
+    def is2d(self) -> bool:
+        return self.kind == "fan2d"
+
+    @property
+    def vol_shape(self):
+        return (self.ny, self.nx) if self.is2d else (self.nz, self.ny, self.nx)
+
+    @property
+    def sino_shape(self):
+        return (self.nview, self.nu) if self.is2d else (self.nview, self.nv, self.nu)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.ct_geometry_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch_of(t: torch.Tensor, inner: Sequence[int], what: str) -> int:
+    k = len(inner)
+    if tuple(t.shape[-k:]) != tuple(inner):
+        raise ValueError(f"{what}: trailing shape {tuple(t.shape[-k:])} != {tuple(inner)}")
+    return int(np.prod(t.shape[:-k], dtype=np.int64)) if t.dim() > k else 1
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_tensor(t: torch.Tensor, what: str):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (no CPU path)")
+    if t.dtype not in DTYPES:
+        raise ValueError(f"{what}: dtype {t.dtype} not supported (float32, float16, bfloat16)")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+
+
+def forward_into(geom: Geometry, x: torch.Tensor, y: torch.Tensor, projector: str = "sf",
+                 mode: str = "proj", stream=None) -> torch.Tensor:
+    """y = A x into a preallocated sinogram tensor (Sec. 2.3, Eq. 1)."""
+    _check_tensor(x, "volume")
+    _check_tensor(y, "sinogram")
+    b = _batch_of(x, geom.vol_shape, "volume")
+    if _batch_of(y, geom.sino_shape, "sinogram") != b:
+        raise ValueError("volume and sinogram batch sizes differ")
+    _check(load().ct_forward(geom.handle, PROJECTORS[projector], MODES[mode], DTYPES[x.dtype],
+                             x.data_ptr(), DTYPES[y.dtype], y.data_ptr(), b, _stream_ptr(stream)))
+    return y
+
+
+def back_into(geom: Geometry, y: torch.Tensor, x: torch.Tensor, projector: str = "sf",
+              mode: str = "proj", stream=None) -> torch.Tensor:
+    """x = A^T y into a preallocated volume tensor (Sec. 2.3, Eq. 2)."""
+    _check_tensor(y, "sinogram")
+    _check_tensor(x, "volume")
+    b = _batch_of(y, geom.sino_shape, "sinogram")
+    if _batch_of(x, geom.vol_shape, "volume") != b:
+        raise ValueError("volume and sinogram batch sizes differ")
+    _check(load().ct_back(geom.handle, PROJECTORS[projector], MODES[mode], DTYPES[y.dtype],
+                          y.data_ptr(), DTYPES[x.dtype], x.data_ptr(), b, _stream_ptr(stream)))
+    return x
+
+
+def forward(geom: Geometry, x: torch.Tensor, projector: str = "sf", mode: str = "proj",
+            out_dtype: Optional[torch.dtype] = None, stream=None) -> torch.Tensor:
+    """y = A x; x: (..., nz, ny, nx) (2D: (..., ny, nx)); y: (..., nview, nv, nu)."""
+    _check_tensor(x, "volume")
+    lead = x.shape[:-len(geom.vol_shape)]
+    y = torch.empty(tuple(lead) + geom.sino_shape, dtype=out_dtype or x.dtype, device=x.device)
+    return forward_into(geom, x, y, projector, mode, stream)
+
+
+def back(geom: Geometry, y: torch.Tensor, projector: str = "sf", mode: str = "proj",
+         out_dtype: Optional[torch.dtype] = None, stream=None) -> torch.Tensor:
+    """x = A^T y; y: (..., nview, nv, nu) (2D: (..., nview, nu)); x: (..., nz, ny, nx)."""
+    _check_tensor(y, "sinogram")
+    lead = y.shape[:-len(geom.sino_shape)]
+    x = torch.empty(tuple(lead) + geom.vol_shape, dtype=out_dtype or y.dtype, device=y.device)
+    return back_into(geom, y, x, projector, mode, stream)

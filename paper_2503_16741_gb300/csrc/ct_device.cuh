@@ -1,0 +1,211 @@
+// ct_device.cuh -- device helpers shared by the projector kernels: storage
+// conversion, detector mapping in local (cell-relative) coordinates, the SF
+// trapezoid integral, interval overlaps and the forward-gather search.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "ct_types.h"
+
+namespace ctp {
+
+// ---------------------------------------------------------------- storage
+template <typename T> __device__ __forceinline__ float ld(const T *__restrict__ p, size_t i);
+template <> __device__ __forceinline__ float ld<float>(const float *__restrict__ p, size_t i) {
+    return __ldg(p + i);
+}
+template <> __device__ __forceinline__ float ld<__half>(const __half *__restrict__ p, size_t i) {
+    return __half2float(__ldg(p + i));
+}
+template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16 *__restrict__ p,
+                                                               size_t i) {
+    return __bfloat162float(__ldg(p + i));
+}
+
+// out_t: 0 = f32, 1 = f16, 2 = bf16; one rounding at the store
+__device__ __forceinline__ void st(void *out, size_t i, float v, int out_t) {
+    if (out_t == 0)
+        static_cast<float *>(out)[i] = v;
+    else if (out_t == 1)
+        static_cast<__half *>(out)[i] = __float2half_rn(v);
+    else
+        static_cast<__nv_bfloat16 *>(out)[i] = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------- intervals
+__device__ __forceinline__ float overlap(float lo1, float hi1, float lo2, float hi2) {
+    return fmaxf(fminf(hi1, hi2) - fmaxf(lo1, lo2), 0.f);
+}
+
+// Integral from -inf to x of the unit ramp that rises from 0 at 0 to 1 at e
+// and stays 1 after it; e = 0 is the unit step.  No division by a vanishing e.
+__device__ __forceinline__ float ramp_int(float x, float e) {
+    float xc = fminf(fmaxf(x, 0.f), e);
+    return fmaf(xc * xc, 0.5f / fmaxf(e, 1e-30f), fmaxf(x - e, 0.f));
+}
+
+// Unit-height trapezoid with knots k0 <= k1 <= k2 <= k3 (cell units), and
+// its integral over cell [d - 1/2, d + 1/2]: the SF transaxial weight.
+struct Trap {
+    float k0, k1, k2, k3;
+};
+__device__ __forceinline__ float trap_G(const Trap &t, float u) {
+    return ramp_int(u - t.k0, t.k1 - t.k0) - ramp_int(u - t.k2, t.k3 - t.k2);
+}
+__device__ __forceinline__ float trap_cell(const Trap &t, int d) {
+    float u = (float)d;
+    return trap_G(t, u + 0.5f) - trap_G(t, u - 0.5f);
+}
+
+__device__ __forceinline__ void cswap(float &a, float &b) {
+    float lo = fminf(a, b), hi = fmaxf(a, b);
+    a = lo;
+    b = hi;
+}
+__device__ __forceinline__ void sort4(float &a, float &b, float &c, float &d) {
+    cswap(a, b);
+    cswap(c, d);
+    cswap(a, c);
+    cswap(b, d);
+    cswap(b, c);
+}
+
+// ---------------------------------------------------------------- detector map
+// (a, b, c) = (w.e_u, w.n, w.e_v) of a point; fractional cell coordinates.
+template <bool CURVED> struct Det {
+    __device__ static __forceinline__ float fu(const CtView &V, float a, float b) {
+        return CURVED ? fmaf(V.Ku, atan2f(a, b), V.Cu) : fmaf(V.Ku, a / b, V.Cu);
+    }
+    // "depth" that divides w.e_v: w.n (flat) or the distance from the source axis (curved)
+    __device__ static __forceinline__ float den(float a, float b) {
+        return CURVED ? sqrtf(fmaf(a, a, b * b)) : b;
+    }
+    // fu(a + da, b + db) - fu(a, b), formed from the small offsets directly
+    __device__ static __forceinline__ float dfu(const CtView &V, float a, float b, float da, float db) {
+        float num = fmaf(da, b, -a * db);
+        if (CURVED) return V.Ku * atan2f(num, fmaf(a + da, a, (b + db) * b));
+        return V.Ku * num / ((b + db) * b);
+    }
+    // ratio (w.e_u)/(w.n) at which fu equals F (for the forward search planes)
+    __device__ static __forceinline__ float ratio_at(const CtView &V, float F) {
+        float t = (F - V.Cu) / V.Ku;
+        return CURVED ? tanf(t) : t;
+    }
+};
+
+// nearest cell to a fractional coordinate, and the remainder in [-1/2, 1/2)
+__device__ __forceinline__ void split_cell(float f, int &ref, float &frac) {
+    float r = floorf(f + 0.5f);
+    ref = (int)r;
+    frac = f - r;
+}
+
+// ---------------------------------------------------------------- forward search
+// Candidate lateral/axial index box of slab s for the detector window
+// fu in [Flo, Fhi], fv in [Glo, Ghi] of a flat detector: the window's four
+// corner rays cut the slab plane in a quadrilateral whose bounding box holds
+// every voxel centre that projects into the window.
+struct SlabCoef {
+    float ul, uk, us, u3;  // au along (lateral, k, slab, const)
+    float nl, nk, ns, n3;  // an
+    float vl, vk, vs, v3;  // av
+};
+__device__ __forceinline__ SlabCoef slab_coef(const CtView &V, int main_y) {
+    SlabCoef c;
+    if (main_y) {
+        c.ul = V.au[0]; c.us = V.au[1];
+        c.nl = V.an[0]; c.ns = V.an[1];
+        c.vl = V.av[0]; c.vs = V.av[1];
+    } else {
+        c.ul = V.au[1]; c.us = V.au[0];
+        c.nl = V.an[1]; c.ns = V.an[0];
+        c.vl = V.av[1]; c.vs = V.av[0];
+    }
+    c.uk = V.au[2]; c.u3 = V.au[3];
+    c.nk = V.an[2]; c.n3 = V.an[3];
+    c.vk = V.av[2]; c.v3 = V.av[3];
+    return c;
+}
+
+// Flat detector: corners of {Ku au - (F-Cu) an = 0} x {Kv av - (G-Cv) an = 0}
+__device__ __forceinline__ bool search_flat(const CtView &V, const SlabCoef &c, int s, float Flo,
+                                            float Fhi, float Glo, float Ghi, int nlat, int nk,
+                                            int &l0, int &l1, int &k0, int &k1) {
+    float lmin = 3.0e38f, lmax = -3.0e38f, kmin = 3.0e38f, kmax = -3.0e38f;
+    float fs = (float)s;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        float tu = (q ? Fhi : Flo) - V.Cu;
+        float Pl = fmaf(V.Ku, c.ul, -tu * c.nl);
+        float Pk = fmaf(V.Ku, c.uk, -tu * c.nk);
+        float Pc = fmaf(V.Ku, fmaf(c.us, fs, c.u3), -tu * fmaf(c.ns, fs, c.n3));
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float tv = (r ? Ghi : Glo) - V.Cv;
+            float Ql = fmaf(V.Kv, c.vl, -tv * c.nl);
+            float Qk = fmaf(V.Kv, c.vk, -tv * c.nk);
+            float Qc = fmaf(V.Kv, fmaf(c.vs, fs, c.v3), -tv * fmaf(c.ns, fs, c.n3));
+            float det = fmaf(Pl, Qk, -Pk * Ql);
+            float l = fmaf(-Pc, Qk, Qc * Pk) / det;
+            float k = fmaf(-Qc, Pl, Pc * Ql) / det;
+            lmin = fminf(lmin, l); lmax = fmaxf(lmax, l);
+            kmin = fminf(kmin, k); kmax = fmaxf(kmax, k);
+        }
+    }
+    l0 = max(0, (int)ceilf(lmin));
+    l1 = min(nlat - 1, (int)floorf(lmax));
+    k0 = max(0, (int)ceilf(kmin));
+    k1 = min(nk - 1, (int)floorf(kmax));
+    return l0 <= l1 && k0 <= k1 && isfinite(lmin) && isfinite(lmax);
+}
+
+// Curved detector (circular geometry, e_v = z): the u window is cut by two
+// vertical planes through the source; the v window by two cones, bounded with
+// the extreme distances of the candidate columns from the source axis.
+__device__ __forceinline__ bool search_curved(const CtView &V, const SlabCoef &c, int s, float Flo,
+                                              float Fhi, float Glo, float Ghi, int nlat, int nk,
+                                              int &l0, int &l1, int &k0, int &k1) {
+    float fs = (float)s;
+    float Bu = fmaf(c.us, fs, c.u3), Bn = fmaf(c.ns, fs, c.n3);
+    float T1 = Det<true>::ratio_at(V, Flo), T2 = Det<true>::ratio_at(V, Fhi);
+    float la = (T1 * Bn - Bu) / (c.ul - T1 * c.nl);
+    float lb = (T2 * Bn - Bu) / (c.ul - T2 * c.nl);
+    l0 = max(0, (int)ceilf(fminf(la, lb)));
+    l1 = min(nlat - 1, (int)floorf(fmaxf(la, lb)));
+    if (l0 > l1) return false;
+    float fl0 = (float)l0, fl1 = (float)l1;
+    float a0 = fmaf(c.ul, fl0, Bu), b0 = fmaf(c.nl, fl0, Bn);
+    float a1 = fmaf(c.ul, fl1, Bu), b1 = fmaf(c.nl, fl1, Bn);
+    float r0 = sqrtf(fmaf(a0, a0, b0 * b0)), r1 = sqrtf(fmaf(a1, a1, b1 * b1));
+    float rmax = fmaxf(r0, r1), rmin = fminf(r0, r1);
+    float g2 = fmaf(c.ul, c.ul, c.nl * c.nl);
+    float ls = -fmaf(c.ul, Bu, c.nl * Bn) / g2;  // closest approach to the axis
+    if (ls > fl0 && ls < fl1) {
+        float as = fmaf(c.ul, ls, Bu), bs = fmaf(c.nl, ls, Bn);
+        rmin = sqrtf(fmaf(as, as, bs * bs));
+    }
+    rmin *= 0.9999f;  // rounding guard on the bound
+    rmax *= 1.0001f;
+    float tlo = (Glo - V.Cv) / V.Kv, thi = (Ghi - V.Cv) / V.Kv;
+    float cmin = fminf(tlo * rmin, tlo * rmax), cmax = fmaxf(thi * rmin, thi * rmax);
+    // w.e_v = vk k + v3 (+ lateral/slab terms, zero when e_v = z)
+    float cb = fmaf(c.vs, fs, c.v3);
+    float ka = (cmin - cb) / c.vk, kb = (cmax - cb) / c.vk;
+    k0 = max(0, (int)ceilf(fminf(ka, kb)));
+    k1 = min(nk - 1, (int)floorf(fmaxf(ka, kb)));
+    return k0 <= k1;
+}
+
+template <bool CURVED>
+__device__ __forceinline__ bool slab_search(const CtView &V, const SlabCoef &c, int s, float Flo,
+                                            float Fhi, float Glo, float Ghi, int nlat, int nk,
+                                            int &l0, int &l1, int &k0, int &k1) {
+    if (CURVED) return search_curved(V, c, s, Flo, Fhi, Glo, Ghi, nlat, nk, l0, l1, k0, k1);
+    return search_flat(V, c, s, Flo, Fhi, Glo, Ghi, nlat, nk, l0, l1, k0, k1);
+}
+
+// rounding guard added to every search window (cells)
+constexpr float kSearchPad = 2e-3f;
+
+}  // namespace ctp

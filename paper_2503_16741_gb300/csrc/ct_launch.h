@@ -1,0 +1,20 @@
+// ct_launch.h -- internal kernel launchers, one per projector.
+// dir: 0 = forward (volume -> sinogram), 1 = back (sinogram -> volume).
+// in_t / out_t: 0 f32, 1 f16, 2 bf16.  All launches are asynchronous on st.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ct_types.h"
+
+namespace ctp {
+
+cudaError_t launch_sf(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                      int out_t, void *out, int batch, cudaStream_t st);
+cudaError_t launch_dd(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                      int out_t, void *out, int batch, cudaStream_t st);
+cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                         int out_t, void *out, int batch, cudaStream_t st);
+cudaError_t launch_ray(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                       int out_t, void *out, int batch, cudaStream_t st);
+
+}  // namespace ctp

@@ -1,0 +1,361 @@
+// k_ray.cu -- ray-driven projector (Siddon 1985, cited in Sec. 2.3): the
+// weight of voxel j for cell c is the length of the source-to-cell-centre
+// segment inside voxel j (half-open voxel boxes).
+// Forward: one thread per ray walks the voxel grid from plane crossing to
+// plane crossing (parameters measured from the volume entry point).
+// Back: the adjoint in gather form -- one thread per voxel column; for each
+// view the cells whose central ray can meet the voxel are found from the
+// voxel's projected bounding box, and each ray's chord through the voxel is
+// computed by the slab method in coordinates centred on the voxel.
+#include "ct_device.cuh"
+#include "ct_launch.h"
+
+namespace ctp {
+
+// world direction from the source to the centre of cell (a, b)
+template <bool CURVED>
+__device__ __forceinline__ void ray_dir(const CtView &V, const CtGrid &g, int a, int b, float d[3]) {
+    const float Vb = g.dv * ((float)b - V.Cv);
+    float cn_, cu_;
+    if (CURVED) {
+        float sg, cg;
+        sincosf(((float)a - V.Cu) / V.Ku, &sg, &cg);
+        cn_ = V.D * cg;
+        cu_ = V.D * sg;
+    } else {
+        cn_ = V.D;
+        cu_ = g.du * ((float)a - V.Cu);
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) d[m] = fmaf(cn_, V.nn[m], fmaf(cu_, V.eu[m], Vb * V.ev[m]));
+}
+
+// ------------------------------------------------------------ forward
+template <typename TIn, bool CURVED>
+__global__ void __launch_bounds__(256)
+ray_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
+        void *__restrict__ sino, int out_t, int tiles_u) {
+    int bx = blockIdx.x;
+    const int tu = bx % tiles_u; bx /= tiles_u;
+    const int v = bx % g.nview;
+    const int bt = bx / g.nview;
+    const int a = tu * 32 + threadIdx.x;
+    const int b = blockIdx.y * 8 + threadIdx.y;
+    if (a >= g.nu || b >= g.nv) return;
+    const CtView &V = views[v];
+    float d[3];
+    ray_dir<CURVED>(V, g, a, b, d);
+    const float len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+    const float h[3] = {g.dx, g.dy, g.dz};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    // source and direction in voxel-index units; voxel i spans [i - 1/2, i + 1/2)
+    float S[3], D[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        S[m] = -V.o[m] / h[m];
+        D[m] = d[m] / h[m];
+    }
+    float tin = 0.f, tout = 1.f;
+    bool hit = true;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const float lo = -0.5f, hi = (float)n[m] - 0.5f;
+        if (D[m] == 0.f) {
+            if (!(S[m] >= lo && S[m] < hi)) hit = false;
+        } else {
+            const float t1 = (lo - S[m]) / D[m], t2 = (hi - S[m]) / D[m];
+            tin = fmaxf(tin, fminf(t1, t2));
+            tout = fminf(tout, fmaxf(t1, t2));
+        }
+    }
+    float acc = 0.f;
+    if (hit && tout > tin) {
+        const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
+        // walk from the entry point q; parameters t are measured from it
+        float q[3], tn[3], inv[3];
+        int cur[3], stp[3];
+        const float T = tout - tin;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            q[m] = fmaf(tin, D[m], S[m]);
+            if (D[m] > 0.f) {
+                cur[m] = (int)floorf(q[m] + 0.5f);
+                stp[m] = 1;
+            } else if (D[m] < 0.f) {
+                cur[m] = (int)ceilf(q[m] - 0.5f);
+                stp[m] = -1;
+            } else {
+                cur[m] = (int)floorf(q[m] + 0.5f);
+                stp[m] = 0;
+            }
+            cur[m] = min(max(cur[m], 0), n[m] - 1);
+            inv[m] = D[m] != 0.f ? 1.f / D[m] : 0.f;
+            tn[m] = D[m] != 0.f ? ((float)cur[m] + 0.5f * (float)stp[m] - q[m]) * inv[m] : 3.0e38f;
+        }
+        float tc = 0.f;
+        const size_t sy = (size_t)g.nx, sz = (size_t)g.nx * g.ny;
+        // every pass steps one axis, so nx + ny + nz + 1 passes cover any ray
+        const int max_steps = n[0] + n[1] + n[2] + 1;
+        for (int it = 0; it < max_steps && tc < T; ++it) {
+            int m = 0;
+            float tnext = tn[0];
+            if (tn[1] < tnext) { m = 1; tnext = tn[1]; }
+            if (tn[2] < tnext) { m = 2; tnext = tn[2]; }
+            const float te = fminf(fmaxf(tnext, tc), T);
+            acc = fmaf(te - tc, ld(x, (size_t)cur[2] * sz + (size_t)cur[1] * sy + (size_t)cur[0]), acc);
+            tc = te;
+            cur[m] += stp[m];
+            if (cur[m] < 0 || cur[m] >= n[m]) break;
+            tn[m] = ((float)cur[m] + 0.5f * (float)stp[m] - q[m]) * inv[m];
+        }
+        acc *= len;
+    }
+    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+}
+
+// ------------------------------------------------------------ back (gather)
+// chord of the ray through voxel (centre X, half extents hx, hy, hz) given
+// its offset e from the centre (world) and unit direction dh
+__device__ __forceinline__ float chord(const float e[3], const float dh[3], const float hh[3]) {
+    float lo = -3.0e38f, hi = 3.0e38f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        if (dh[m] == 0.f) {
+            if (!(e[m] >= -hh[m] && e[m] < hh[m])) return 0.f;
+        } else {
+            const float inv = 1.f / dh[m];
+            const float t1 = (-hh[m] - e[m]) * inv, t2 = (hh[m] - e[m]) * inv;
+            lo = fmaxf(lo, fminf(t1, t2));
+            hi = fminf(hi, fmaxf(t1, t2));
+        }
+    }
+    return fmaxf(hi - lo, 0.f);
+}
+
+// offset, at the voxel's depth, of the central ray of cell (a, b) from the
+// voxel centre, formed from the cell-relative positions (a - fu), (b - fv)
+template <bool CURVED>
+__device__ __forceinline__ float ray_weight(const CtView &V, const CtGrid &g, int a, int b, float dfu,
+                                            float dfv, float cn, float rho, const float hh[3]) {
+    float d[3], e[3];
+    ray_dir<CURVED>(V, g, a, b, d);
+    const float il = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+    float dh[3] = {d[0] * il, d[1] * il, d[2] * il};
+    if (CURVED) {
+        // dfu = a - fu (cells): angle of the voxel centre from the ray plane
+        const float dg = -dfu / V.Ku;
+        float sg, cg;
+        sincosf(((float)a - V.Cu) / V.Ku, &sg, &cg);
+        float sd, cd;
+        sincosf(dg, &sd, &cd);
+        const float s2 = sinf(0.5f * dg);
+        const float lat = -rho * sd;  // along m_perp = cos(ga) e_u - sin(ga) n
+        const float vert = (rho / V.D) * g.dv * (dfv - 2.f * s2 * s2 * ((float)b - V.Cv));
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+            e[m] = fmaf(lat, fmaf(cg, V.eu[m], -sg * V.nn[m]), vert * V.ev[m]);
+    } else {
+        const float sc = cn / V.D;
+        const float eu = sc * g.du * dfu, ev = sc * g.dv * dfv;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) e[m] = fmaf(eu, V.eu[m], ev * V.ev[m]);
+    }
+    return chord(e, dh, hh);
+}
+
+template <typename TIn, bool CURVED, int ZT>
+__global__ void __launch_bounds__(128)
+ray_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
+              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
+    int bx = blockIdx.x;
+    const int tx = bx % tiles_x; bx /= tiles_x;
+    const int kc = bx % nzc;
+    const int bt = bx / nzc;
+    const int i = tx * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int kbeg = kc * ZT;
+    float acc[ZT];
+#pragma unroll
+    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    const float hh[3] = {0.5f * g.dx, 0.5f * g.dy, 0.5f * g.dz};
+    const size_t vstride = (size_t)g.nv * g.nu;
+    const TIn *ys = sino + (size_t)bt * g.nview * vstride;
+    const float fi = (float)i, fj = (float)j;
+    for (int v = 0; v < g.nview; ++v) {
+        const CtView &V = views[v];
+        const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
+        const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, V.an[3]));
+        int aref;
+        float fr;
+        split_cell(Det<CURVED>::fu(V, cu, cn), aref, fr);
+        // u extent of the column's shadow: its four corners
+        const float hxu = 0.5f * V.au[0], hxn = 0.5f * V.an[0];
+        const float hyu = 0.5f * V.au[1], hyn = 0.5f * V.an[1];
+        float t0 = Det<CURVED>::dfu(V, cu, cn, -hxu - hyu, -hxn - hyn);
+        float t1 = Det<CURVED>::dfu(V, cu, cn, hxu - hyu, hxn - hyn);
+        float t2 = Det<CURVED>::dfu(V, cu, cn, -hxu + hyu, -hxn + hyn);
+        float t3 = Det<CURVED>::dfu(V, cu, cn, hxu + hyu, hxn + hyn);
+        const float umin = fr + fminf(fminf(t0, t1), fminf(t2, t3));
+        const float umax = fr + fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
+        int d0 = (int)ceilf(umin - kSearchPad), d1 = (int)floorf(umax + kSearchPad);
+        d0 = max(d0, -aref);
+        d1 = min(d1, g.nu - 1 - aref);
+        if (d0 > d1) continue;
+        // depth range of the column (flat: w.n over the square; curved: rho)
+        const float rho = Det<CURVED>::den(cu, cn);
+        float dmin, dmax;
+        if (CURVED) {
+            const float hd = 0.5f * sqrtf(g.dx * g.dx + g.dy * g.dy);
+            dmin = rho - hd;
+            dmax = rho + hd;
+        } else {
+            const float hd = fabsf(hxn) + fabsf(hyn);
+            dmin = cn - hd;
+            dmax = cn + hd;
+        }
+        const TIn *yv = ys + (size_t)v * vstride;
+#pragma unroll
+        for (int kk = 0; kk < ZT; ++kk) {
+            const int k = kbeg + kk;
+            if (k >= g.nz) break;
+            const float cv = fmaf(V.av[2], (float)k, V.av[3]);
+            const float fv = fmaf(V.Kv, cv / rho, V.Cv);
+            const float hz = 0.5f * fabsf(V.av[2]);
+            const float c1 = cv - hz, c2 = cv + hz;
+            const float vmin = fmaf(V.Kv, fminf(c1 / dmin, c1 / dmax), V.Cv);
+            const float vmax = fmaf(V.Kv, fmaxf(c2 / dmin, c2 / dmax), V.Cv);
+            const int b0 = max(0, (int)ceilf(vmin - kSearchPad));
+            const int b1 = min(g.nv - 1, (int)floorf(vmax + kSearchPad));
+            float s = 0.f;
+            for (int b = b0; b <= b1; ++b) {
+                const TIn *row = yv + (size_t)b * g.nu;
+                for (int d = d0; d <= d1; ++d) {
+                    const int a = aref + d;
+                    const float w = ray_weight<CURVED>(V, g, a, b, (float)d - fr, (float)b - fv, cn, rho, hh);
+                    if (w > 0.f) s = fmaf(w, ld(row, (size_t)a), s);
+                }
+            }
+            acc[kk] += s;
+        }
+    }
+    const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
+#pragma unroll
+    for (int kk = 0; kk < ZT; ++kk) {
+        const int k = kbeg + kk;
+        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+    }
+}
+
+template <typename TIn, int ZT>
+__global__ void __launch_bounds__(128)
+ray_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
+            void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
+    int bx = blockIdx.x;
+    const int tx = bx % tiles_x; bx /= tiles_x;
+    const int kc = bx % nzc;
+    const int bt = bx / nzc;
+    const int i = tx * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int kbeg = kc * ZT;
+    float acc[ZT];
+#pragma unroll
+    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    const float hh[3] = {0.5f * g.dx, 0.5f * g.dy, 0.5f * g.dz};
+    const size_t vstride = (size_t)g.nv * g.nu;
+    const TIn *ys = sino + (size_t)bt * g.nview * vstride;
+    const float fi = (float)i, fj = (float)j;
+    for (int v = 0; v < g.nview; ++v) {
+        const CtView &V = views[v];
+        const TIn *yv = ys + (size_t)v * vstride;
+#pragma unroll
+        for (int kk = 0; kk < ZT; ++kk) {
+            const int k = kbeg + kk;
+            if (k >= g.nz) break;
+            const float fk = (float)k;
+            const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, fmaf(V.au[2], fk, V.au[3])));
+            const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, fmaf(V.an[2], fk, V.an[3])));
+            const float cv = fmaf(V.av[0], fi, fmaf(V.av[1], fj, fmaf(V.av[2], fk, V.av[3])));
+            int aref, bref;
+            float fr, vr;
+            split_cell(fmaf(V.Ku, cu / cn, V.Cu), aref, fr);
+            split_cell(fmaf(V.Kv, cv / cn, V.Cv), bref, vr);
+            // shadow of the box: its eight corners
+            float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float sx = (c & 1) ? 0.5f : -0.5f, sy = (c & 2) ? 0.5f : -0.5f;
+                const float sz = (c & 4) ? 0.5f : -0.5f;
+                const float du_ = fmaf(sx, V.au[0], fmaf(sy, V.au[1], sz * V.au[2]));
+                const float dn_ = fmaf(sx, V.an[0], fmaf(sy, V.an[1], sz * V.an[2]));
+                const float dv_ = fmaf(sx, V.av[0], fmaf(sy, V.av[1], sz * V.av[2]));
+                const float pu = fmaf(V.Ku, fmaf(du_, cn, -cu * dn_) / ((cn + dn_) * cn), fr);
+                const float pv = fmaf(V.Kv, fmaf(dv_, cn, -cv * dn_) / ((cn + dn_) * cn), vr);
+                umin = fminf(umin, pu); umax = fmaxf(umax, pu);
+                vmin = fminf(vmin, pv); vmax = fmaxf(vmax, pv);
+            }
+            int d0 = max((int)ceilf(umin - kSearchPad), -aref);
+            int d1 = min((int)floorf(umax + kSearchPad), g.nu - 1 - aref);
+            int e0 = max((int)ceilf(vmin - kSearchPad), -bref);
+            int e1 = min((int)floorf(vmax + kSearchPad), g.nv - 1 - bref);
+            float s = 0.f;
+            for (int e = e0; e <= e1; ++e) {
+                const int b = bref + e;
+                const TIn *row = yv + (size_t)b * g.nu;
+                for (int d = d0; d <= d1; ++d) {
+                    const int a = aref + d;
+                    const float w = ray_weight<false>(V, g, a, b, (float)d - fr, (float)e - vr, cn, cn, hh);
+                    if (w > 0.f) s = fmaf(w, ld(row, (size_t)a), s);
+                }
+            }
+            acc[kk] += s;
+        }
+    }
+    const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
+#pragma unroll
+    for (int kk = 0; kk < ZT; ++kk) {
+        const int k = kbeg + kk;
+        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+namespace {
+constexpr int kZT = 8;
+
+template <typename TIn>
+cudaError_t ray_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
+                         int out_t, int batch, cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    if (dir == 0) {
+        const int tiles_u = (g.nu + 31) / 32;
+        dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
+        if (g.variant == GEO_CIRC_CURVED)
+            ray_fwd<TIn, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        else
+            ray_fwd<TIn, false><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+    } else {
+        const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+        dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+        if (g.variant == GEO_NONCIRC_FLAT)
+            ray_back_nc<TIn, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        else if (g.variant == GEO_CIRC_CURVED)
+            ray_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        else
+            ray_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_ray(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                       int out_t, void *out, int batch, cudaStream_t st) {
+    switch (in_t) {
+    case 0: return ray_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
+    case 1: return ray_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
+    default: return ray_launch_t<__nv_bfloat16>(dir, g, views, in, out, out_t, batch, st);
+    }
+}
+
+}  // namespace ctp

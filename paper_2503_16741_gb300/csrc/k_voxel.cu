@@ -1,0 +1,259 @@
+// k_voxel.cu -- voxel-driven projector (Peters 1981, cited in Sec. 2.3).
+// A voxel is a point at its centre; it is projected to the detector and
+// shared between the 2 (2D) or 4 (3D) nearest cells with bilinear weights.
+// The amplitude spreads the voxel's mass over the local ray density:
+//   3D  A = dx dy dz r D^2 / (rho^3 du dv)      2D  A = dx dy r D / (rho^2 du)
+// with r = |X - s|, rho = (X - s).n (flat) or the distance of X from the
+// source axis (curved), D = source-detector distance (radius if curved).
+// The back kernel is the classic voxel-driven backprojector; the forward
+// kernel is its exact adjoint in gather form.
+#include "ct_device.cuh"
+#include "ct_launch.h"
+
+namespace ctp {
+
+// circular geometry: column quantities shared down z
+struct VxCol {
+    float fu;         // fractional u of the column (all z)
+    float sv, fv0;    // fv of voxel k: sv * k + fv0
+    float rxy2, den;  // w_x^2 + w_y^2 and the depth rho
+};
+
+template <bool CURVED>
+__device__ __forceinline__ VxCol vx_col(const CtView &V, const CtGrid &g, int i, int j) {
+    const float fi = (float)i, fj = (float)j;
+    const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
+    const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, V.an[3]));
+    VxCol C;
+    C.fu = Det<CURVED>::fu(V, cu, cn);
+    C.den = Det<CURVED>::den(cu, cn);
+    C.sv = V.Kv * V.av[2] / C.den;
+    C.fv0 = fmaf(V.Kv, V.av[3] / C.den, V.Cv);
+    const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
+    C.rxy2 = fmaf(wx, wx, wy * wy);
+    return C;
+}
+
+__device__ __forceinline__ float vx_amp(const CtGrid &g, const CtView &V, float r, float den) {
+    if (g.is2d) return (g.dx * g.dy / g.du) * r * V.D / (den * den);
+    const float q = V.D / den;
+    return (g.dx * g.dy * g.dz / (g.du * g.dv)) * (r / den) * q * q;
+}
+
+__device__ __forceinline__ float vx_amp_col(const VxCol &C, const CtGrid &g, const CtView &V, int k) {
+    const float wz = fmaf((float)k, g.dz, V.o[2]);
+    return vx_amp(g, V, sqrtf(fmaf(wz, wz, C.rxy2)), C.den);
+}
+
+// non-circular: per voxel
+struct VxVox {
+    float fu, fv, amp;
+};
+__device__ __forceinline__ VxVox vx_vox_nc(const CtView &V, const CtGrid &g, int i, int j, int k) {
+    const float fi = (float)i, fj = (float)j, fk = (float)k;
+    const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, fmaf(V.au[2], fk, V.au[3])));
+    const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, fmaf(V.an[2], fk, V.an[3])));
+    const float cv = fmaf(V.av[0], fi, fmaf(V.av[1], fj, fmaf(V.av[2], fk, V.av[3])));
+    VxVox P;
+    P.fu = fmaf(V.Ku, cu / cn, V.Cu);
+    P.fv = fmaf(V.Kv, cv / cn, V.Cv);
+    const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
+    const float wz = fmaf(fk, g.dz, V.o[2]);
+    P.amp = vx_amp(g, V, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))), cn);
+    return P;
+}
+
+// hat weight of cell c for fractional position f: 1 - t at floor(f), t at floor(f)+1
+__device__ __forceinline__ float hat(float f, int c) {
+    const float f0 = floorf(f);
+    const int d = c - (int)f0;
+    const float t = f - f0;
+    return d == 0 ? 1.f - t : (d == 1 ? t : 0.f);
+}
+
+// ------------------------------------------------------------ back (gather)
+template <typename TIn>
+__device__ __forceinline__ float bilinear(const TIn *yv, const CtGrid &g, float fu, float fv) {
+    const float a0f = floorf(fu), b0f = floorf(fv);
+    const int a0 = (int)a0f, b0 = (int)b0f;
+    const float ta = fu - a0f, tb = fv - b0f;
+    float s = 0.f;
+#pragma unroll
+    for (int db = 0; db < 2; ++db) {
+        const int b = b0 + db;
+        if (b < 0 || b >= g.nv) continue;
+        const float hb = db ? tb : 1.f - tb;
+        const TIn *row = yv + (size_t)b * g.nu;
+        float r = 0.f;
+        if (a0 >= 0 && a0 < g.nu) r = (1.f - ta) * ld(row, (size_t)a0);
+        if (a0 + 1 >= 0 && a0 + 1 < g.nu) r = fmaf(ta, ld(row, (size_t)(a0 + 1)), r);
+        s = fmaf(hb, r, s);
+    }
+    return s;
+}
+
+template <typename TIn, bool CURVED, int ZT>
+__global__ void __launch_bounds__(128)
+vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
+             void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
+    int bx = blockIdx.x;
+    const int tx = bx % tiles_x; bx /= tiles_x;
+    const int kc = bx % nzc;
+    const int bt = bx / nzc;
+    const int i = tx * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int kbeg = kc * ZT;
+    float acc[ZT];
+#pragma unroll
+    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    const size_t vstride = (size_t)g.nv * g.nu;
+    const TIn *ys = sino + (size_t)bt * g.nview * vstride;
+    for (int v = 0; v < g.nview; ++v) {
+        const CtView &V = views[v];
+        const VxCol C = vx_col<CURVED>(V, g, i, j);
+        if (C.fu <= -1.f || C.fu >= (float)g.nu) continue;
+        const TIn *yv = ys + (size_t)v * vstride;
+#pragma unroll
+        for (int kk = 0; kk < ZT; ++kk) {
+            const int k = kbeg + kk;
+            if (k >= g.nz) break;
+            const float fv = fmaf(C.sv, (float)k, C.fv0);
+            acc[kk] = fmaf(vx_amp_col(C, g, V, k), bilinear(yv, g, C.fu, fv), acc[kk]);
+        }
+    }
+    const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
+#pragma unroll
+    for (int kk = 0; kk < ZT; ++kk) {
+        const int k = kbeg + kk;
+        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+    }
+}
+
+template <typename TIn, int ZT>
+__global__ void __launch_bounds__(128)
+vx_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
+           void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
+    int bx = blockIdx.x;
+    const int tx = bx % tiles_x; bx /= tiles_x;
+    const int kc = bx % nzc;
+    const int bt = bx / nzc;
+    const int i = tx * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int kbeg = kc * ZT;
+    float acc[ZT];
+#pragma unroll
+    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    const size_t vstride = (size_t)g.nv * g.nu;
+    const TIn *ys = sino + (size_t)bt * g.nview * vstride;
+    for (int v = 0; v < g.nview; ++v) {
+        const CtView &V = views[v];
+        const TIn *yv = ys + (size_t)v * vstride;
+#pragma unroll
+        for (int kk = 0; kk < ZT; ++kk) {
+            const int k = kbeg + kk;
+            if (k >= g.nz) break;
+            const VxVox P = vx_vox_nc(V, g, i, j, k);
+            acc[kk] = fmaf(P.amp, bilinear(yv, g, P.fu, P.fv), acc[kk]);
+        }
+    }
+    const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
+#pragma unroll
+    for (int kk = 0; kk < ZT; ++kk) {
+        const int k = kbeg + kk;
+        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+    }
+}
+
+// ------------------------------------------------------------ forward (gather)
+// Cell (a, b) receives voxels whose centre projects within one cell of it.
+template <typename TIn, int VARIANT>
+__global__ void __launch_bounds__(256)
+vx_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
+       void *__restrict__ sino, int out_t, int tiles_u) {
+    constexpr bool CURVED = VARIANT == GEO_CIRC_CURVED;
+    int bx = blockIdx.x;
+    const int tu = bx % tiles_u; bx /= tiles_u;
+    const int v = bx % g.nview;
+    const int bt = bx / g.nview;
+    const int a = tu * 32 + threadIdx.x;
+    const int b = blockIdx.y * 8 + threadIdx.y;
+    if (a >= g.nu || b >= g.nv) return;
+    const CtView &V = views[v];
+    const int main_y = V.main_y;
+    const SlabCoef sc = slab_coef(V, main_y);
+    const float m = 1.0f + kSearchPad;
+    const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
+    const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
+    float acc = 0.f;
+    for (int s = 0; s < nslab; ++s) {
+        int l0, l1, k0, k1;
+        if (!slab_search<CURVED>(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1))
+            continue;
+        for (int l = l0; l <= l1; ++l) {
+            const int i = main_y ? l : s, j = main_y ? s : l;
+            if (VARIANT == GEO_NONCIRC_FLAT) {
+                for (int k = k0; k <= k1; ++k) {
+                    const VxVox P = vx_vox_nc(V, g, i, j, k);
+                    const float w = hat(P.fu, a) * hat(P.fv, b);
+                    if (w == 0.f) continue;
+                    acc = fmaf(P.amp * w, ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
+                }
+            } else {
+                const VxCol C = vx_col<CURVED>(V, g, i, j);
+                const float wa = hat(C.fu, a);
+                if (wa == 0.f) continue;
+                for (int k = k0; k <= k1; ++k) {
+                    const float wb = hat(fmaf(C.sv, (float)k, C.fv0), b);
+                    if (wb == 0.f) continue;
+                    acc = fmaf(vx_amp_col(C, g, V, k) * wa * wb,
+                               ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
+                }
+            }
+        }
+    }
+    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+}
+
+// ------------------------------------------------------------ launchers
+namespace {
+constexpr int kZT = 8;
+
+template <typename TIn>
+cudaError_t vx_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
+                        int out_t, int batch, cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    if (dir == 0) {
+        const int tiles_u = (g.nu + 31) / 32;
+        dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
+        if (g.variant == GEO_NONCIRC_FLAT)
+            vx_fwd<TIn, GEO_NONCIRC_FLAT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        else if (g.variant == GEO_CIRC_CURVED)
+            vx_fwd<TIn, GEO_CIRC_CURVED><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        else
+            vx_fwd<TIn, GEO_CIRC_FLAT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+    } else {
+        const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+        dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+        if (g.variant == GEO_NONCIRC_FLAT)
+            vx_back_nc<TIn, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        else if (g.variant == GEO_CIRC_CURVED)
+            vx_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        else
+            vx_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                         int out_t, void *out, int batch, cudaStream_t st) {
+    switch (in_t) {
+    case 0: return vx_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
+    case 1: return vx_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
+    default: return vx_launch_t<__nv_bfloat16>(dir, g, views, in, out, out_t, batch, st);
+    }
+}
+
+}  // namespace ctp

@@ -1,0 +1,130 @@
+"""GPU (CUDA, through the C ABI) versus the FP64 oracle on seeded inputs.
+
+FP32 storage must match within relative L2 1e-5 (the bound the FP32 path is
+held to); the pair must satisfy the adjoint identity in FP32 to 1e-5."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import workloads as W
+from gpu_util import GEOMS, PROJECTORS, TOL_F32, ragged, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ct():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_16741_gb300 as ct
+    ct.load()
+    return ct
+
+
+def _gpu(ct, spec):
+    return ct.Geometry.from_spec(spec)
+
+
+def ct_vol_shape(spec):
+    return (spec.ny, spec.nx) if spec.kind == "fan2d" else (spec.nz, spec.ny, spec.nx)
+
+
+def ct_sino_shape(spec):
+    return (spec.nview, spec.nu) if spec.kind == "fan2d" else (spec.nview, spec.nv, spec.nu)
+
+
+@pytest.mark.parametrize("proj", PROJECTORS)
+@pytest.mark.parametrize("kind,det", GEOMS)
+def test_forward_matches_oracle(ct, kind, det, proj):
+    spec = ragged(kind, det)
+    x = W.phantom(spec, seed=1)
+    ref = oracle.forward(spec, proj, x)
+    g = _gpu(ct, spec)
+    y = ct.forward(g, torch.as_tensor(x.reshape(ct_vol_shape(spec)), dtype=torch.float32).cuda(), proj)
+    torch.cuda.synchronize()
+    err = rel_l2(y.cpu().numpy().reshape(ref.shape), ref)
+    assert np.linalg.norm(ref) > 0
+    assert err <= TOL_F32, f"{kind}/{det}/{proj}: rel L2 {err:.3e}"
+
+
+@pytest.mark.parametrize("proj", PROJECTORS)
+@pytest.mark.parametrize("kind,det", GEOMS)
+def test_back_matches_oracle(ct, kind, det, proj):
+    spec = ragged(kind, det)
+    y = W.random_sino(spec, seed=2)[0]
+    ref = oracle.back(spec, proj, y)
+    g = _gpu(ct, spec)
+    x = ct.back(g, torch.as_tensor(y.reshape(ct_sino_shape(spec)), dtype=torch.float32).cuda(), proj)
+    torch.cuda.synchronize()
+    err = rel_l2(x.cpu().numpy().reshape(ref.shape), ref)
+    assert err <= TOL_F32, f"{kind}/{det}/{proj}: rel L2 {err:.3e}"
+
+
+@pytest.mark.parametrize("proj", PROJECTORS)
+@pytest.mark.parametrize("kind,det", GEOMS)
+def test_adjoint_identity_fp32(ct, kind, det, proj):
+    spec = ragged(kind, det, seed=3)
+    g = _gpu(ct, spec)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.rand(ct_vol_shape(spec), generator=gen, device="cuda")
+    y = torch.rand(ct_sino_shape(spec), generator=gen, device="cuda")
+    Ax = ct.forward(g, x, proj)
+    Aty = ct.back(g, y, proj)
+    lhs = float((Ax.double() * y.double()).sum())
+    rhs = float((x.double() * Aty.double()).sum())
+    assert abs(lhs - rhs) <= TOL_F32 * abs(lhs), f"{lhs} vs {rhs}"
+
+
+@pytest.mark.parametrize("proj", PROJECTORS)
+def test_batch_items_independent_and_deterministic(ct, proj):
+    spec = ragged("circ3d", "flat", seed=4)
+    g = _gpu(ct, spec)
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    x = torch.rand((2, 3) + ct_vol_shape(spec), generator=gen, device="cuda")
+    y = ct.forward(g, x, proj)
+    for b in range(2):
+        for c in range(3):
+            assert torch.equal(y[b, c], ct.forward(g, x[b, c].contiguous(), proj))
+    assert torch.equal(y, ct.forward(g, x, proj))
+    s = torch.rand((2,) + ct_sino_shape(spec), generator=gen, device="cuda")
+    xb = ct.back(g, s, proj)
+    assert torch.equal(xb[1], ct.back(g, s[1].contiguous(), proj))
+
+
+@pytest.mark.parametrize("proj", PROJECTORS)
+def test_view_subset_equals_slice(ct, proj):
+    """Ordered subsets: a geometry of selected views gives those views."""
+    spec = ragged("noncirc3d", "flat", seed=6)
+    x = torch.as_tensor(W.phantom(spec, seed=2), dtype=torch.float32).cuda()
+    full = ct.forward(_gpu(ct, spec), x, proj)
+    views = [0, 5, 17, 22]
+    sub = ct.forward(_gpu(ct, spec.subset(views)), x, proj)
+    assert torch.equal(sub, full[views])
+
+
+def test_degenerate_sizes(ct):
+    """Single voxel, single cell, single view."""
+    spec = W.GeometrySpec("circ3d", "flat", 1, 1, 1, 2.0, 2.0, 2.0, 1, 1, 3.0, 3.0, 1,
+                          theta=0.3, sad=100.0, sdd=200.0)
+    g = _gpu(ct, spec)
+    for proj in PROJECTORS:
+        x = torch.ones((1, 1, 1), device="cuda")
+        y = ct.forward(g, x, proj)
+        ref = oracle.forward(spec, proj, np.ones((1, 1, 1)))
+        assert rel_l2(y.cpu().numpy(), ref) <= TOL_F32
+        xb = ct.back(g, torch.ones((1, 1, 1), device="cuda"), proj)
+        refb = oracle.back(spec, proj, np.ones((1, 1, 1)))
+        assert rel_l2(xb.cpu().numpy(), refb) <= TOL_F32
+
+
+def test_volume_outside_detector_gives_zero(ct):
+    """A detector offset so far that no ray meets the volume: all zeros."""
+    spec = W.GeometrySpec("circ3d", "flat", 8, 8, 8, 1.0, 1.0, 1.0, 16, 16, 1.0, 1.0, 3,
+                          theta=[0.0, 1.0, 2.0], sad=200.0, sdd=400.0, u_ofst=500.0)
+    g = _gpu(ct, spec)
+    x = torch.ones((8, 8, 8), device="cuda")
+    for proj in PROJECTORS:
+        assert float(ct.forward(g, x, proj).abs().max()) == 0.0
+        assert float(ct.back(g, torch.ones((3, 16, 16), device="cuda"), proj).abs().max()) == 0.0

@@ -244,21 +244,32 @@ def _phantom_numpy(spec, params, ndim):
     hz = spec.nz * spec.dz / 2.0
     xs = _grid_coords(nx, spec.dx) / hx
     ys = _grid_coords(ny, spec.dy) / hy
+    zs = _grid_coords(nz, spec.dz) / hz if ndim == 3 else np.zeros(1)
     out = np.zeros((nz, ny, nx))
-    if ndim == 2:
-        X, Y = np.meshgrid(xs, ys, indexing="xy")
-        for c, a, rot, val in params:
-            p = np.stack([X - c[0], Y - c[1]], -1) @ rot
-            m = ((p / a) ** 2).sum(-1) <= 1.0
-            out[0][m] = val
-        return out
-    zs = _grid_coords(nz, spec.dz) / hz
-    Y, X = np.meshgrid(ys, xs, indexing="ij")
     for c, a, rot, val in params:
-        for k in range(nz):
-            p = np.stack([X - c[0], Y - c[1], np.full_like(X, zs[k] - c[2])], -1) @ rot
-            m = ((p / a) ** 2).sum(-1) <= 1.0
-            out[k][m] = val
+        # bounding box of the body (half extent along axis i: |R_i. * a|)
+        ext = np.sqrt(((rot * a[None, :]) ** 2).sum(1))
+        cz = c[2] if ndim == 3 else 0.0
+        ez = ext[2] if ndim == 3 else 1.0
+        ix = np.nonzero(np.abs(xs - c[0]) <= ext[0] + 1e-12)[0]
+        iy = np.nonzero(np.abs(ys - c[1]) <= ext[1] + 1e-12)[0]
+        iz = np.nonzero(np.abs(zs - cz) <= ez + 1e-12)[0] if ndim == 3 else np.zeros(1, int)
+        if ix.size == 0 or iy.size == 0 or iz.size == 0:
+            continue
+        X = xs[ix][None, None, :] - c[0]
+        Y = ys[iy][None, :, None] - c[1]
+        if ndim == 2:
+            p0 = X * rot[0, 0] + Y * rot[1, 0]
+            p1 = X * rot[0, 1] + Y * rot[1, 1]
+            m = (p0 / a[0]) ** 2 + (p1 / a[1]) ** 2 <= 1.0
+        else:
+            Z = zs[iz][:, None, None] - cz
+            p0 = X * rot[0, 0] + Y * rot[1, 0] + Z * rot[2, 0]
+            p1 = X * rot[0, 1] + Y * rot[1, 1] + Z * rot[2, 1]
+            p2 = X * rot[0, 2] + Y * rot[1, 2] + Z * rot[2, 2]
+            m = (p0 / a[0]) ** 2 + (p1 / a[1]) ** 2 + (p2 / a[2]) ** 2 <= 1.0
+        sub = out[iz[0]:iz[-1] + 1, iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1]
+        sub[np.broadcast_to(m, sub.shape)] = val
     return out
 
 
@@ -268,31 +279,27 @@ def _phantom_torch(spec, params, ndim, device, dtype):
     f64 = torch.float64
     hx = spec.nx * spec.dx / 2.0
     hy = spec.ny * spec.dy / 2.0
+    hz = spec.nz * spec.dz / 2.0
     xs = torch.as_tensor(_grid_coords(nx, spec.dx) / hx, dtype=f64, device=device)
     ys = torch.as_tensor(_grid_coords(ny, spec.dy) / hy, dtype=f64, device=device)
+    zs = (torch.as_tensor(_grid_coords(nz, spec.dz) / hz, dtype=f64, device=device)
+          if ndim == 3 else torch.zeros(1, dtype=f64, device=device))
     out = torch.zeros((nz, ny, nx), dtype=f64, device=device)
-    if ndim == 2:
-        Y, X = torch.meshgrid(ys, xs, indexing="ij")
-        for c, a, rot, val in params:
-            R = torch.as_tensor(rot, dtype=f64, device=device)
-            p = torch.stack([X - c[0], Y - c[1]], -1) @ R
-            m = ((p / torch.as_tensor(a, dtype=f64, device=device)) ** 2).sum(-1) <= 1.0
-            out[0][m] = val
-        return out.to(dtype)
-    hz = spec.nz * spec.dz / 2.0
-    zs = torch.as_tensor(_grid_coords(nz, spec.dz) / hz, dtype=f64, device=device)
-    Y, X = torch.meshgrid(ys, xs, indexing="ij")
     for c, a, rot, val in params:
-        R = torch.as_tensor(rot, dtype=f64, device=device)
-        A = torch.as_tensor(a, dtype=f64, device=device)
-        for k0 in range(0, nz, 64):
-            k1 = min(nz, k0 + 64)
-            Z = zs[k0:k1].view(-1, 1, 1) - c[2]
-            p = torch.stack([(X - c[0]).expand(k1 - k0, ny, nx),
-                             (Y - c[1]).expand(k1 - k0, ny, nx),
-                             Z.expand(k1 - k0, ny, nx)], -1) @ R
-            m = ((p / A) ** 2).sum(-1) <= 1.0
-            out[k0:k1][m] = val
+        cz = c[2] if ndim == 3 else 0.0
+        X = (xs - c[0]).view(1, 1, -1)
+        Y = (ys - c[1]).view(1, -1, 1)
+        if ndim == 2:
+            p0 = X * rot[0, 0] + Y * rot[1, 0]
+            p1 = X * rot[0, 1] + Y * rot[1, 1]
+            m = (p0 / a[0]) ** 2 + (p1 / a[1]) ** 2 <= 1.0
+        else:
+            Z = (zs - cz).view(-1, 1, 1)
+            p0 = X * rot[0, 0] + Y * rot[1, 0] + Z * rot[2, 0]
+            p1 = X * rot[0, 1] + Y * rot[1, 1] + Z * rot[2, 1]
+            p2 = X * rot[0, 2] + Y * rot[1, 2] + Z * rot[2, 2]
+            m = (p0 / a[0]) ** 2 + (p1 / a[1]) ** 2 + (p2 / a[2]) ** 2 <= 1.0
+        out[m.expand(nz, ny, nx)] = val
     return out.to(dtype)
 
 
