@@ -97,7 +97,7 @@ class ClockSampler:
             return None
         sm = sorted(float(r[1]) for r in rows)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]),
                 "reasons": reasons, "samples": len(rows),
                 "power_w_max": max(float(r[3]) for r in rows)}

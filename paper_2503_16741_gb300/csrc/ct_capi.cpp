@@ -249,6 +249,12 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
     G.is2d = two_d ? 1 : 0;
     G.variant = d->kind == CT_NONCIRC3D ? ctp::GEO_NONCIRC_FLAT
                                         : (curved ? ctp::GEO_CIRC_CURVED : ctp::GEO_CIRC_FLAT);
+    G.max_m_sf_u = 0.f;
+    G.max_m_dd_u = 0.f;
+    for (const CtView &V : g->host_views) {
+        G.max_m_sf_u = std::max(G.max_m_sf_u, V.m_sf_u);
+        G.max_m_dd_u = std::max(G.max_m_dd_u, V.m_dd_u);
+    }
 
     if (cudaGetDevice(&g->device) != cudaSuccess) {
         delete g;

@@ -57,6 +57,15 @@ __device__ __forceinline__ float trap_cell(const Trap &t, int d) {
     float u = (float)d;
     return trap_G(t, u + 0.5f) - trap_G(t, u - 0.5f);
 }
+// trapezoid weights of the 4 cells d0 .. d0+3 (zero past d1), sharing the
+// antiderivative at their common edges; each equals trap_cell(t, d0 + q)
+__device__ __forceinline__ void trap_cells4(const Trap &t, int d0, int d1, float F[4]) {
+    float G[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) G[q] = trap_G(t, (float)(d0 + q) - 0.5f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) F[q] = (d0 + q <= d1) ? G[q + 1] - G[q] : 0.f;
+}
 
 __device__ __forceinline__ void cswap(float &a, float &b) {
     float lo = fminf(a, b), hi = fmaxf(a, b);
@@ -82,10 +91,11 @@ template <bool CURVED> struct Det {
         return CURVED ? sqrtf(fmaf(a, a, b * b)) : b;
     }
     // fu(a + da, b + db) - fu(a, b), formed from the small offsets directly
+    // (a difference of about one cell: the fast division's 2 ulp are ~1e-7 cell)
     __device__ static __forceinline__ float dfu(const CtView &V, float a, float b, float da, float db) {
         float num = fmaf(da, b, -a * db);
         if (CURVED) return V.Ku * atan2f(num, fmaf(a + da, a, (b + db) * b));
-        return V.Ku * num / ((b + db) * b);
+        return V.Ku * __fdividef(num, (b + db) * b);
     }
     // ratio (w.e_u)/(w.n) at which fu equals F (for the forward search planes)
     __device__ static __forceinline__ float ratio_at(const CtView &V, float F) {
@@ -160,38 +170,46 @@ __device__ __forceinline__ bool search_flat(const CtView &V, const SlabCoef &c, 
     return l0 <= l1 && k0 <= k1 && isfinite(lmin) && isfinite(lmax);
 }
 
-// Curved detector (circular geometry, e_v = z): the u window is cut by two
-// vertical planes through the source; the v window by two cones, bounded with
-// the extreme distances of the candidate columns from the source axis.
-__device__ __forceinline__ bool search_curved(const CtView &V, const SlabCoef &c, int s, float Flo,
-                                              float Fhi, float Glo, float Ghi, int nlat, int nk,
-                                              int &l0, int &l1, int &k0, int &k1) {
-    float fs = (float)s;
-    float Bu = fmaf(c.us, fs, c.u3), Bn = fmaf(c.ns, fs, c.n3);
-    float T1 = Det<true>::ratio_at(V, Flo), T2 = Det<true>::ratio_at(V, Fhi);
-    float la = (T1 * Bn - Bu) / (c.ul - T1 * c.nl);
-    float lb = (T2 * Bn - Bu) / (c.ul - T2 * c.nl);
+// Circular geometry (e_v = z, e_u and n horizontal): the u window is cut by
+// two vertical planes through the source axis; the v window by two planes
+// (flat) or cones (curved) through the source, bounded with the extreme
+// depths of the candidate columns.
+template <bool CURVED>
+__device__ __forceinline__ bool search_circ(const CtView &V, const SlabCoef &c, int s, float Flo,
+                                            float Fhi, float Glo, float Ghi, int nlat, int nk,
+                                            int &l0, int &l1, int &k0, int &k1) {
+    const float fs = (float)s;
+    const float Bu = fmaf(c.us, fs, c.u3), Bn = fmaf(c.ns, fs, c.n3);
+    const float T1 = Det<CURVED>::ratio_at(V, Flo), T2 = Det<CURVED>::ratio_at(V, Fhi);
+    const float la = (T1 * Bn - Bu) / (c.ul - T1 * c.nl);
+    const float lb = (T2 * Bn - Bu) / (c.ul - T2 * c.nl);
     l0 = max(0, (int)ceilf(fminf(la, lb)));
     l1 = min(nlat - 1, (int)floorf(fmaxf(la, lb)));
     if (l0 > l1) return false;
-    float fl0 = (float)l0, fl1 = (float)l1;
-    float a0 = fmaf(c.ul, fl0, Bu), b0 = fmaf(c.nl, fl0, Bn);
-    float a1 = fmaf(c.ul, fl1, Bu), b1 = fmaf(c.nl, fl1, Bn);
-    float r0 = sqrtf(fmaf(a0, a0, b0 * b0)), r1 = sqrtf(fmaf(a1, a1, b1 * b1));
-    float rmax = fmaxf(r0, r1), rmin = fminf(r0, r1);
-    float g2 = fmaf(c.ul, c.ul, c.nl * c.nl);
-    float ls = -fmaf(c.ul, Bu, c.nl * Bn) / g2;  // closest approach to the axis
-    if (ls > fl0 && ls < fl1) {
-        float as = fmaf(c.ul, ls, Bu), bs = fmaf(c.nl, ls, Bn);
-        rmin = sqrtf(fmaf(as, as, bs * bs));
+    const float fl0 = (float)l0, fl1 = (float)l1;
+    const float b0 = fmaf(c.nl, fl0, Bn), b1 = fmaf(c.nl, fl1, Bn);
+    float rmin, rmax;
+    if (CURVED) {
+        const float a0 = fmaf(c.ul, fl0, Bu), a1 = fmaf(c.ul, fl1, Bu);
+        const float r0 = sqrtf(fmaf(a0, a0, b0 * b0)), r1 = sqrtf(fmaf(a1, a1, b1 * b1));
+        rmax = fmaxf(r0, r1);
+        rmin = fminf(r0, r1);
+        const float g2 = fmaf(c.ul, c.ul, c.nl * c.nl);
+        const float ls = -fmaf(c.ul, Bu, c.nl * Bn) / g2;  // closest approach to the axis
+        if (ls > fl0 && ls < fl1) {
+            const float as = fmaf(c.ul, ls, Bu), bs = fmaf(c.nl, ls, Bn);
+            rmin = sqrtf(fmaf(as, as, bs * bs));
+        }
+    } else {
+        rmin = fminf(b0, b1);
+        rmax = fmaxf(b0, b1);
     }
     rmin *= 0.9999f;  // rounding guard on the bound
     rmax *= 1.0001f;
-    float tlo = (Glo - V.Cv) / V.Kv, thi = (Ghi - V.Cv) / V.Kv;
-    float cmin = fminf(tlo * rmin, tlo * rmax), cmax = fmaxf(thi * rmin, thi * rmax);
-    // w.e_v = vk k + v3 (+ lateral/slab terms, zero when e_v = z)
-    float cb = fmaf(c.vs, fs, c.v3);
-    float ka = (cmin - cb) / c.vk, kb = (cmax - cb) / c.vk;
+    const float tlo = (Glo - V.Cv) / V.Kv, thi = (Ghi - V.Cv) / V.Kv;
+    const float cmin = fminf(tlo * rmin, tlo * rmax), cmax = fmaxf(thi * rmin, thi * rmax);
+    // w.e_v = vk k + v3 (e_v = z: no lateral or slab term)
+    const float ka = (cmin - c.v3) / c.vk, kb = (cmax - c.v3) / c.vk;
     k0 = max(0, (int)ceilf(fminf(ka, kb)));
     k1 = min(nk - 1, (int)floorf(fmaxf(ka, kb)));
     return k0 <= k1;
@@ -201,8 +219,7 @@ template <bool CURVED>
 __device__ __forceinline__ bool slab_search(const CtView &V, const SlabCoef &c, int s, float Flo,
                                             float Fhi, float Glo, float Ghi, int nlat, int nk,
                                             int &l0, int &l1, int &k0, int &k1) {
-    if (CURVED) return search_curved(V, c, s, Flo, Fhi, Glo, Ghi, nlat, nk, l0, l1, k0, k1);
-    return search_flat(V, c, s, Flo, Fhi, Glo, Ghi, nlat, nk, l0, l1, k0, k1);
+    return search_circ<CURVED>(V, c, s, Flo, Fhi, Glo, Ghi, nlat, nk, l0, l1, k0, k1);
 }
 
 // rounding guard added to every search window (cells)

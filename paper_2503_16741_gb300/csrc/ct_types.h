@@ -44,6 +44,8 @@ struct CtGrid {
     float du, dv;
     int is2d;          // fan beam: single slice, unit slice thickness and row height
     int variant;       // GeoVariant
+    float max_m_sf_u;  // largest per-view SF transaxial footprint bound (cells)
+    float max_m_dd_u;  // largest per-view DD boundary bound (cells)
 };
 
 }  // namespace ctp

@@ -94,66 +94,145 @@ __device__ __forceinline__ SfVox sf_vox_nc(const CtView &V, const CtGrid &g, int
 
 // ------------------------------------------------------------ back (gather)
 // Thread = one voxel column (i, j) over a z-chunk of ZT voxels; loops over
-// all views; reads the 1-4 cells x 1-3 rows of each voxel's footprint.
+// all views (records staged in shared memory, kViews at a time).
+// Common case (footprint <= 4 cells, axial rectangle shorter than a row):
+// the column's 4 transaxial weights filter each detector row the chunk
+// touches once, R(b) = sum_q Fu[q] y[b][a0 + q], into a per-thread slice of
+// shared memory; each voxel then takes its two rows, x += amp (Fv0 R(b0) +
+// Fv1 R(b0 + 1)).  Other footprints take the general loops.  Both evaluate
+// the same weights as the forward kernel.
+constexpr int kViews = 64;
+
+__device__ __forceinline__ void stage_views(CtView *dst, const CtView *__restrict__ src, int n, int tid,
+                                            int nthr) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    constexpr int W = sizeof(CtView) / sizeof(float4);
+    for (int t = tid; t < n * W; t += nthr) d4[t] = __ldg(s4 + t);
+}
+
+__device__ __forceinline__ float sf_amp_fast(float invm, float rxy2, float wz) {
+    const float t = fmaf(wz, wz, rxy2);
+    return invm * t * rsqrtf(t);
+}
+
 template <typename TIn, bool CURVED, int ZT>
 __global__ void __launch_bounds__(128)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
+    constexpr int NR = ZT + 4;  // rows one chunk can touch (|sv| < 1), with a guard row each side
+    __shared__ CtView sview[kViews];
+    __shared__ float Rs[NR][128];
+    __shared__ float Gs[ZT][128];  // general-path partial sums (thread-private slots)
     int bx = blockIdx.x;
     const int tx = bx % tiles_x; bx /= tiles_x;
     const int kc = bx % nzc;
     const int bt = bx / nzc;
     const int i = tx * 32 + threadIdx.x;
     const int j = blockIdx.y * 4 + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const bool active = i < g.nx && j < g.ny;
     const int kbeg = kc * ZT;
+    const int kend = min(kbeg + ZT, g.nz);
     float acc[ZT];
 #pragma unroll
-    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    for (int q = 0; q < ZT; ++q) {
+        acc[q] = 0.f;
+        Gs[q][tid] = 0.f;
+    }
     const size_t vstride = (size_t)g.nv * g.nu;
     const TIn *ys = sino + (size_t)bt * g.nview * vstride;
-    for (int v = 0; v < g.nview; ++v) {
-        const CtView &V = views[v];
-        const SfCol C = sf_col<CURVED>(V, g, i, j);
-        int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
-        d0 = max(d0, -C.aref);
-        d1 = min(d1, g.nu - 1 - C.aref);
-        const TIn *yv = ys + (size_t)v * vstride;
-        for (int db = d0; db <= d1; db += 4) {
-            float Fu[4];
+    for (int v0 = 0; v0 < g.nview; v0 += kViews) {
+        const int nvc = min(kViews, g.nview - v0);
+        __syncthreads();
+        stage_views(sview, views + v0, nvc, tid, 128);
+        __syncthreads();
+        if (!active) continue;
+        for (int vv = 0; vv < nvc; ++vv) {
+            const CtView &V = sview[vv];
+            const SfCol C = sf_col<CURVED>(V, g, i, j);
+            int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
+            d0 = max(d0, -C.aref);
+            d1 = min(d1, g.nu - 1 - C.aref);
+            if (d0 > d1) continue;
+            const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
+            if (d1 - d0 <= 3 && C.hv < 0.5f) {
+                float Fu[4];
+                trap_cells4(C.T, d0, d1, Fu);
+                int ai[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) Fu[q] = (db + q <= d1) ? trap_cell(C.T, db + q) : 0.f;
-            const int abase = C.aref + db;
-            const int na = min(4, d1 - db + 1);
-#pragma unroll
-            for (int kk = 0; kk < ZT; ++kk) {
-                const int k = kbeg + kk;
-                if (k >= g.nz) break;
-                int bref;
-                float vf;
-                split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
-                e0 = max(e0, -bref);
-                e1 = min(e1, g.nv - 1 - bref);
-                float s = 0.f;
-                for (int e = e0; e <= e1; ++e) {
-                    const float Fv = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
-                    const TIn *row = yv + (size_t)(bref + e) * g.nu + abase;
-                    float r = Fu[0] * ld(row, 0);
-                    if (na > 1) r = fmaf(Fu[1], ld(row, 1), r);
-                    if (na > 2) r = fmaf(Fu[2], ld(row, 2), r);
-                    if (na > 3) r = fmaf(Fu[3], ld(row, 3), r);
-                    s = fmaf(Fv, r, s);
+                for (int q = 0; q < 4; ++q) ai[q] = C.aref + (d0 + q <= d1 ? d0 + q : d0);
+                // rows touched by the chunk, one guard row each side
+                const float fa = fmaf(C.sv, (float)kbeg, C.fv0), fb = fmaf(C.sv, (float)(kend - 1), C.fv0);
+                const int rb0 = (int)floorf(fminf(fa, fb) - C.hv + 0.5f) - 1;
+                const int nr = min(NR, (int)floorf(fmaxf(fa, fb) + C.hv + 0.5f) + 2 - rb0);
+                for (int r = 0; r < nr; ++r) {
+                    const int b = rb0 + r;
+                    float R = 0.f;
+                    if (b >= 0 && b < g.nv) {
+                        const TIn *row = yv + (size_t)b * g.nu;
+                        R = Fu[0] * ld(row, ai[0]);
+                        R = fmaf(Fu[1], ld(row, ai[1]), R);
+                        R = fmaf(Fu[2], ld(row, ai[2]), R);
+                        R = fmaf(Fu[3], ld(row, ai[3]), R);
+                    }
+                    Rs[r][tid] = R;
                 }
-                acc[kk] = fmaf(sf_amp(C, g, V, k), s, acc[kk]);
+#pragma unroll
+                for (int kk = 0; kk < ZT; ++kk) {
+                    const int k = kbeg + kk;
+                    if (k < kend) {
+                        int bref;
+                        float vf;
+                        split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                        const float lo = vf - C.hv, hi = vf + C.hv;
+                        const int e0 = (int)floorf(lo + 0.5f);
+                        const float Fv0 = overlap(lo, hi, e0 - 0.5f, e0 + 0.5f);
+                        const float Fv1 = overlap(lo, hi, e0 + 0.5f, e0 + 1.5f);
+                        const int r0 = min(max(bref + e0 - rb0, 0), nr - 2);
+                        const float wz = fmaf((float)k, g.dz, V.o[2]);
+                        acc[kk] = fmaf(sf_amp_fast(C.invm, C.rxy2, wz),
+                                       fmaf(Fv0, Rs[r0][tid], Fv1 * Rs[r0 + 1][tid]), acc[kk]);
+                    }
+                }
+                continue;
+            }
+            for (int db = d0; db <= d1; db += 4) {
+                float Fu[4];
+                trap_cells4(C.T, db, d1, Fu);
+                const int abase = C.aref + db;
+                const int na = min(4, d1 - db + 1);
+                for (int kk = 0; kk < ZT; ++kk) {
+                    const int k = kbeg + kk;
+                    if (k >= kend) break;
+                    int bref;
+                    float vf;
+                    split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                    int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
+                    e0 = max(e0, -bref);
+                    e1 = min(e1, g.nv - 1 - bref);
+                    float s = 0.f;
+                    for (int e = e0; e <= e1; ++e) {
+                        const float Fv = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
+                        const TIn *row = yv + (size_t)(bref + e) * g.nu + abase;
+                        float r = Fu[0] * ld(row, 0);
+                        if (na > 1) r = fmaf(Fu[1], ld(row, 1), r);
+                        if (na > 2) r = fmaf(Fu[2], ld(row, 2), r);
+                        if (na > 3) r = fmaf(Fu[3], ld(row, 3), r);
+                        s = fmaf(Fv, r, s);
+                    }
+                    const float wz = fmaf((float)k, g.dz, V.o[2]);
+                    Gs[kk][tid] = fmaf(sf_amp_fast(C.invm, C.rxy2, wz), s, Gs[kk][tid]);
+                }
             }
         }
     }
+    if (!active) return;
     const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < kend) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk] + Gs[kk][tid], out_t);
     }
 }
 
@@ -216,48 +295,234 @@ sf_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 }
 
 // ------------------------------------------------------------ forward (gather)
-// Thread = one detector cell (a, b) of one view; loops over the slabs of
-// the view's main axis; in each slab only the voxels whose footprint can
-// reach the cell (a window widened by the per-view footprint bound).
-template <typename TIn, bool CURVED>
-__global__ void __launch_bounds__(256)
+// CTA = 32 detector cells x BV = 8 RPT rows of one view, 256 threads.
+// Work items are the voxel columns (slab s, lateral l) whose footprint can
+// reach the tile, taken 256 at a time.  Stage 1: thread = item; it computes
+// the column's transaxial weights Fu (<= 4 cells) and walks the column down
+// z, accumulating its axial projection Z(item, b) = sum_k amp Fv x onto the
+// tile's rows in shared memory.  Stage 2: thread = (cell a, RPT rows); it
+// finds, per slab of the round, the items that reach its cell and adds
+// Fu(item, a) Z(item, b).  Each sum has a fixed order: deterministic, and
+// no atomics.  Used when every footprint spans at most 4 cells (decided on
+// the host from the per-view footprint bound); otherwise sf_fwd_circ_wide.
+constexpr int kItems = 256;
+constexpr int kSlabSeg = 1024;
+
+template <int RPT> struct SfFwdSmem {
+    float Z[kItems][8 * RPT + 1];
+    float Fu[4][kItems];
+    int a0[kItems];
+    int L0[kSlabSeg], cnt[kSlabSeg], off[kSlabSeg + 1];
+};
+
+template <typename TIn, bool CURVED, int RPT>
+__global__ void __launch_bounds__(256, 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
-            void *__restrict__ sino, int out_t, int tiles_u) {
+            void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
+    constexpr int BV = 8 * RPT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SfFwdSmem<RPT> &S = *reinterpret_cast<SfFwdSmem<RPT> *>(smem_raw);
     int bx = blockIdx.x;
     const int tu = bx % tiles_u; bx /= tiles_u;
+    const int tv = bx % tiles_v; bx /= tiles_v;
     const int v = bx % g.nview;
     const int bt = bx / g.nview;
-    const int a = tu * 32 + threadIdx.x;
-    const int b = blockIdx.y * 8 + threadIdx.y;
-    if (a >= g.nu || b >= g.nv) return;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int A0 = tu * 32, B0 = tv * BV;
+    const int a = A0 + threadIdx.x;
     const CtView &V = views[v];
     const int main_y = V.main_y;
     const SlabCoef sc = slab_coef(V, main_y);
     const float mu = V.m_sf_u + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
     const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
     const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
+    const float T1 = Det<CURVED>::ratio_at(V, a - mu), T2 = Det<CURVED>::ratio_at(V, a + mu);
+    float acc[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) acc[r] = 0.f;
+
+    for (int seg = 0; seg < nslab; seg += kSlabSeg) {
+        const int nseg = min(kSlabSeg, nslab - seg);
+        // column range of every slab of the segment for the whole tile
+        __syncthreads();
+        for (int t = tid; t < nseg; t += 256) {
+            int L0, L1, K0, K1, c = 0;
+            if (slab_search<CURVED>(V, sc, seg + t, A0 - mu, A0 + 31.f + mu, B0 - mv, B0 + BV - 1.f + mv,
+                                    nlat, g.nz, L0, L1, K0, K1))
+                c = L1 - L0 + 1;
+            S.L0[t] = L0;
+            S.cnt[t] = c;
+        }
+        __syncthreads();
+        if (tid == 0) {  // exclusive prefix sum (nseg <= 1024, once per segment)
+            int o = 0;
+            for (int t = 0; t < nseg; ++t) { S.off[t] = o; o += S.cnt[t]; }
+            S.off[nseg] = o;
+        }
+        __syncthreads();
+        const int total = S.off[nseg];
+        for (int base = 0; base < total; base += kItems) {
+            // ---- stage 1: one item (column) per thread
+            const int q = base + tid;
+            if (q < total) {
+                int lo = 0, hi = nseg - 1;  // slab of item q: last t with off[t] <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (S.off[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                const int s = seg + lo;
+                const int l = S.L0[lo] + (q - S.off[lo]);
+                const int i = main_y ? l : s, j = main_y ? s : l;
+                const SfCol C = sf_col<CURVED>(V, g, i, j);
+                int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
+                float Fu[4];
+                trap_cells4(C.T, d0, d1, Fu);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) S.Fu[r][tid] = Fu[r];
+                S.a0[tid] = C.aref + d0;
+#pragma unroll
+                for (int r = 0; r < BV; ++r) S.Z[tid][r] = 0.f;
+                // voxels whose axial rectangle can meet a row of the tile
+                const float hw = 0.5f + C.hv + kSearchPad;
+                const float rsv = 1.f / C.sv;
+                const float ka = ((float)B0 - C.fv0 - hw) * rsv;
+                const float kb = ((float)(B0 + BV - 1) - C.fv0 + hw) * rsv;
+                const int k0 = max(0, (int)ceilf(fminf(ka, kb)));
+                const int k1 = min(g.nz - 1, (int)floorf(fmaxf(ka, kb)));
+                const size_t cidx = (size_t)j * g.nx + i, zs = (size_t)g.nx * g.ny;
+                for (int k = k0; k <= k1; ++k) {
+                    int bref;
+                    float vf;
+                    split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                    const float wz = fmaf((float)k, g.dz, V.o[2]);
+                    const float val = sf_amp_fast(C.invm, C.rxy2, wz) * ld(x, (size_t)k * zs + cidx);
+                    const int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
+                    for (int e = e0; e <= e1; ++e) {
+                        const int r = bref + e - B0;
+                        if (r >= 0 && r < BV)
+                            S.Z[tid][r] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[tid][r]);
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- stage 2: thread = (cell a, rows B0 + threadIdx.y + 8 r)
+            if (a < g.nu) {
+                const int qend = min(total, base + kItems);
+                int lo = 0, hi = nseg - 1;  // first slab with items in [base, qend)
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (S.off[mid] <= base) lo = mid; else hi = mid - 1;
+                }
+                for (int t = lo; t < nseg && S.off[t] < qend; ++t) {
+                    if (S.cnt[t] == 0) continue;
+                    const float fs = (float)(seg + t);
+                    const float Bu = fmaf(sc.us, fs, sc.u3), Bn = fmaf(sc.ns, fs, sc.n3);
+                    const float la = (T1 * Bn - Bu) / (sc.ul - T1 * sc.nl);
+                    const float lb = (T2 * Bn - Bu) / (sc.ul - T2 * sc.nl);
+                    const int c0 = max((int)ceilf(fminf(la, lb)) - S.L0[t], 0);
+                    const int c1 = min((int)floorf(fmaxf(la, lb)) - S.L0[t], S.cnt[t] - 1);
+                    for (int c = c0; c <= c1; ++c) {
+                        const int item = S.off[t] + c - base;
+                        if (item < 0 || item >= kItems) continue;
+                        const int d = a - S.a0[item];
+                        if (d < 0 || d > 3) continue;
+                        const float w = S.Fu[d][item];
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[item][threadIdx.y + 8 * r], acc[r]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (a < g.nu) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int b = B0 + threadIdx.y + 8 * r;
+            if (b < g.nv) st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc[r], out_t);
+        }
+    }
+}
+
+// Forward for footprints wider than 4 cells: CTA = 32 x 8 cells; per slab
+// the CTA computes the contexts of the columns that reach its tile once into
+// shared memory; every cell gathers from the columns and voxels reaching it.
+struct SfColS {
+    Trap T;
+    int aref;
+    float sv, fv0, hv, invm, rxy2, rsv;
+};
+constexpr int kCols = 256;
+
+template <typename TIn, bool CURVED>
+__global__ void __launch_bounds__(256)
+sf_fwd_circ_wide(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
+                 void *__restrict__ sino, int out_t, int tiles_u) {
+    __shared__ SfColS cols[kCols];
+    int bx = blockIdx.x;
+    const int tu = bx % tiles_u; bx /= tiles_u;
+    const int v = bx % g.nview;
+    const int bt = bx / g.nview;
+    const int a = tu * 32 + threadIdx.x;
+    const int b = blockIdx.y * 8 + threadIdx.y;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const bool active = a < g.nu && b < g.nv;
+    const CtView &V = views[v];
+    const int main_y = V.main_y;
+    const SlabCoef sc = slab_coef(V, main_y);
+    const float mu = V.m_sf_u + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
+    const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
+    const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
+    const float T1 = Det<CURVED>::ratio_at(V, a - mu), T2 = Det<CURVED>::ratio_at(V, a + mu);
+    const float tile_a = (float)(tu * 32), tile_b = (float)(blockIdx.y * 8);
     float acc = 0.f;
     for (int s = 0; s < nslab; ++s) {
-        int l0, l1, k0, k1;
-        if (!slab_search<CURVED>(V, sc, s, a - mu, a + mu, b - mv, b + mv, nlat, g.nz, l0, l1, k0, k1))
-            continue;
-        for (int l = l0; l <= l1; ++l) {
-            const int i = main_y ? l : s, j = main_y ? s : l;
-            const SfCol C = sf_col<CURVED>(V, g, i, j);
-            const float Fu = trap_cell(C.T, a - C.aref);
-            if (Fu == 0.f) continue;
-            for (int k = k0; k <= k1; ++k) {
-                int bref;
-                float vf;
-                split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                const int e = b - bref;
-                const float Fv = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
-                if (Fv == 0.f) continue;
-                acc = fmaf(sf_amp(C, g, V, k) * Fu * Fv, ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
+        int L0, L1, K0, K1;
+        if (!slab_search<CURVED>(V, sc, s, tile_a - mu, tile_a + 31.f + mu, tile_b - mv, tile_b + 7.f + mv,
+                                 nlat, g.nz, L0, L1, K0, K1))
+            continue;  // uniform over the CTA
+        const float fs = (float)s;
+        const float Bu = fmaf(sc.us, fs, sc.u3), Bn = fmaf(sc.ns, fs, sc.n3);
+        const float la = (T1 * Bn - Bu) / (sc.ul - T1 * sc.nl);
+        const float lb = (T2 * Bn - Bu) / (sc.ul - T2 * sc.nl);
+        const int ml0 = (int)ceilf(fminf(la, lb)), ml1 = (int)floorf(fmaxf(la, lb));
+        for (int cb = L0; cb <= L1; cb += kCols) {
+            const int nc = min(kCols, L1 - cb + 1);
+            __syncthreads();
+            for (int t = tid; t < nc; t += 256) {
+                const int l = cb + t;
+                const SfCol C = sf_col<CURVED>(V, g, main_y ? l : s, main_y ? s : l);
+                SfColS &Q = cols[t];
+                Q.T = C.T; Q.aref = C.aref; Q.sv = C.sv; Q.fv0 = C.fv0; Q.hv = C.hv;
+                Q.invm = C.invm; Q.rxy2 = C.rxy2; Q.rsv = 1.f / C.sv;
+            }
+            __syncthreads();
+            if (!active) continue;
+            const int l0 = max(ml0, cb), l1 = min(ml1, cb + nc - 1);
+            for (int l = l0; l <= l1; ++l) {
+                const SfColS &C = cols[l - cb];
+                const float Fu = trap_cell(C.T, a - C.aref);
+                if (Fu == 0.f) continue;
+                const int i = main_y ? l : s, j = main_y ? s : l;
+                const float hw = 0.5f + C.hv + kSearchPad;
+                const float ka = ((float)b - C.fv0 - hw) * C.rsv, kb = ((float)b - C.fv0 + hw) * C.rsv;
+                const int k0 = max(K0, (int)ceilf(fminf(ka, kb)));
+                const int k1 = min(K1, (int)floorf(fmaxf(ka, kb)));
+                for (int k = k0; k <= k1; ++k) {
+                    int bref;
+                    float vf;
+                    split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                    const int e = b - bref;
+                    const float Fv = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
+                    if (Fv == 0.f) continue;
+                    const float wz = fmaf((float)k, g.dz, V.o[2]);
+                    acc = fmaf(sf_amp_fast(C.invm, C.rxy2, wz) * Fu * Fv,
+                               ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
+                }
             }
         }
     }
-    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+    if (active) st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
 }
 
 template <typename TIn>
@@ -299,7 +564,20 @@ sf_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vo
 
 // ------------------------------------------------------------ launchers
 namespace {
-constexpr int kZT = 8;
+constexpr int kZT = 16;
+
+template <typename TIn, bool CURVED, int RPT>
+cudaError_t sf_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
+                          int batch, cudaStream_t st) {
+    const int tiles_u = (g.nu + 31) / 32, tiles_v = (g.nv + 8 * RPT - 1) / (8 * RPT);
+    const size_t smem = sizeof(SfFwdSmem<RPT>);
+    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, RPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 blk(32, 8), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
+    sf_fwd_circ<TIn, CURVED, RPT><<<grd, blk, smem, st>>>(g, views, src, out, out_t, tiles_u, tiles_v);
+    return cudaGetLastError();
+}
 
 template <typename TIn>
 cudaError_t sf_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
@@ -307,23 +585,38 @@ cudaError_t sf_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
     const TIn *src = static_cast<const TIn *>(in);
     if (dir == 0) {
         const int tiles_u = (g.nu + 31) / 32;
-        dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
-        if (g.variant == GEO_NONCIRC_FLAT)
+        if (g.variant == GEO_NONCIRC_FLAT) {
+            dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
             sf_fwd_nc<TIn><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-        else if (g.variant == GEO_CIRC_CURVED)
-            sf_fwd_circ<TIn, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+            return cudaGetLastError();
+        }
+        // every transaxial footprint spans at most 4 cells when its half
+        // width (bounded per view) is at most 1.5 cells
+        if (g.max_m_sf_u <= 1.5f) {
+            const bool curved = g.variant == GEO_CIRC_CURVED;
+            if (g.nv >= 64)
+                return curved ? sf_fwd_stream<TIn, true, 8>(g, views, src, out, out_t, batch, st)
+                              : sf_fwd_stream<TIn, false, 8>(g, views, src, out, out_t, batch, st);
+            return curved ? sf_fwd_stream<TIn, true, 1>(g, views, src, out, out_t, batch, st)
+                          : sf_fwd_stream<TIn, false, 1>(g, views, src, out, out_t, batch, st);
+        }
+        dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
+        if (g.variant == GEO_CIRC_CURVED)
+            sf_fwd_circ_wide<TIn, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
         else
-            sf_fwd_circ<TIn, false><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-    } else {
-        const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
-        dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-        if (g.variant == GEO_NONCIRC_FLAT)
-            sf_back_nc<TIn, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
-        else if (g.variant == GEO_CIRC_CURVED)
-            sf_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
-        else
-            sf_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+            sf_fwd_circ_wide<TIn, false><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        return cudaGetLastError();
     }
+    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+    dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+    if (g.variant == GEO_NONCIRC_FLAT) {
+        const int nzc8 = (g.nz + 7) / 8;
+        dim3 grd8((unsigned)(tiles_x * nzc8 * batch), (unsigned)((g.ny + 3) / 4));
+        sf_back_nc<TIn, 8><<<grd8, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc8);
+    } else if (g.variant == GEO_CIRC_CURVED)
+        sf_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    else
+        sf_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     return cudaGetLastError();
 }
 }  // namespace

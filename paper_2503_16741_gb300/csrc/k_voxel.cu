@@ -189,8 +189,10 @@ vx_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
     float acc = 0.f;
     for (int s = 0; s < nslab; ++s) {
         int l0, l1, k0, k1;
-        if (!slab_search<CURVED>(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1))
-            continue;
+        const bool hit = VARIANT == GEO_NONCIRC_FLAT
+                             ? search_flat(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1)
+                             : slab_search<CURVED>(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1);
+        if (!hit) continue;
         for (int l = l0; l <= l1; ++l) {
             const int i = main_y ? l : s, j = main_y ? s : l;
             if (VARIANT == GEO_NONCIRC_FLAT) {
