@@ -45,13 +45,24 @@ __device__ __forceinline__ float ramp_int(float x, float e) {
     return fmaf(xc * xc, 0.5f / fmaxf(e, 1e-30f), fmaxf(x - e, 0.f));
 }
 
+// same with the factor 0.5 / max(e, tiny) supplied by the caller
+__device__ __forceinline__ float ramp_int_h(float x, float e, float half_inv_e) {
+    float xc = fminf(fmaxf(x, 0.f), e);
+    return fmaf(xc * xc, half_inv_e, fmaxf(x - e, 0.f));
+}
+
 // Unit-height trapezoid with knots k0 <= k1 <= k2 <= k3 (cell units), and
 // its integral over cell [d - 1/2, d + 1/2]: the SF transaxial weight.
+// h1, h3 = 0.5 / (rise width), 0.5 / (fall width), formed once per trapezoid.
 struct Trap {
     float k0, k1, k2, k3;
+    float h1, h3;
 };
+__device__ __forceinline__ Trap make_trap(float k0, float k1, float k2, float k3) {
+    return Trap{k0, k1, k2, k3, 0.5f / fmaxf(k1 - k0, 1e-30f), 0.5f / fmaxf(k3 - k2, 1e-30f)};
+}
 __device__ __forceinline__ float trap_G(const Trap &t, float u) {
-    return ramp_int(u - t.k0, t.k1 - t.k0) - ramp_int(u - t.k2, t.k3 - t.k2);
+    return ramp_int_h(u - t.k0, t.k1 - t.k0, t.h1) - ramp_int_h(u - t.k2, t.k3 - t.k2, t.h3);
 }
 __device__ __forceinline__ float trap_cell(const Trap &t, int d) {
     float u = (float)d;
@@ -65,6 +76,17 @@ __device__ __forceinline__ void trap_cells4(const Trap &t, int d0, int d1, float
     for (int q = 0; q < 5; ++q) G[q] = trap_G(t, (float)(d0 + q) - 0.5f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) F[q] = (d0 + q <= d1) ? G[q + 1] - G[q] : 0.f;
+}
+
+// Axial rectangle [lo, hi] of width < 1 row (relative to a row grid whose
+// row e covers [e - 1/2, e + 1/2]): it meets rows e0 and e0 + 1 only, with
+// the overlaps below (equal to overlap(lo, hi, e -+ 1/2) bit for bit).
+__device__ __forceinline__ void two_rows(float lo, float hi, int &e0, float &F0, float &F1) {
+    const float ef = floorf(lo + 0.5f);
+    e0 = (int)ef;
+    const float m = ef + 0.5f;
+    F0 = fmaxf(fminf(hi, m) - fmaxf(lo, ef - 0.5f), 0.f);
+    F1 = fmaxf(hi - m, 0.f);
 }
 
 __device__ __forceinline__ void cswap(float &a, float &b) {

@@ -36,14 +36,14 @@ __device__ __forceinline__ SfCol sf_col(const CtView &V, const CtGrid &g, int i,
     float t2 = fr + Det<CURVED>::dfu(V, cu, cn, -hxu + hyu, -hxn + hyn);
     float t3 = fr + Det<CURVED>::dfu(V, cu, cn, hxu + hyu, hxn + hyn);
     sort4(t0, t1, t2, t3);
-    C.T = Trap{t0, t1, t2, t3};
-    const float den = Det<CURVED>::den(cu, cn);
-    C.sv = V.Kv * V.av[2] / den;
-    C.fv0 = fmaf(V.Kv, V.av[3] / den, V.Cv);
+    C.T = make_trap(t0, t1, t2, t3);
+    const float kd = V.Kv / Det<CURVED>::den(cu, cn);
+    C.sv = kd * V.av[2];
+    C.fv0 = fmaf(kd, V.av[3], V.Cv);
     C.hv = 0.5f * fabsf(C.sv);
     const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
     C.rxy2 = fmaf(wx, wx, wy * wy);
-    C.invm = g.dx / fmaxf(fabsf(wx), fabsf(wy));
+    C.invm = __fdividef(g.dx, fmaxf(fabsf(wx), fabsf(wy)));
     return C;
 }
 
@@ -80,7 +80,7 @@ __device__ __forceinline__ SfVox sf_vox_nc(const CtView &V, const CtGrid &g, int
     float t2 = fr + dratio(V.Ku, cu, cn, -hxu + hyu, -hxn + hyn);
     float t3 = fr + dratio(V.Ku, cu, cn, hxu + hyu, hxn + hyn);
     sort4(t0, t1, t2, t3);
-    P.T = Trap{t0, t1, t2, t3};
+    P.T = make_trap(t0, t1, t2, t3);
     const float hzv = 0.5f * V.av[2], hzn = 0.5f * V.an[2];
     const float e1 = vr + dratio(V.Kv, cv, cn, hzv, hzn);
     const float e2 = vr + dratio(V.Kv, cv, cn, -hzv, -hzn);
@@ -117,7 +117,7 @@ __device__ __forceinline__ float sf_amp_fast(float invm, float rxy2, float wz) {
 }
 
 template <typename TIn, bool CURVED, int ZT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 7)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
     constexpr int NR = ZT + 4;  // rows one chunk can touch (|sv| < 1), with a guard row each side
@@ -156,41 +156,50 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             d1 = min(d1, g.nu - 1 - C.aref);
             if (d0 > d1) continue;
             const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
-            if (d1 - d0 <= 3 && C.hv < 0.5f) {
+            if (d1 - d0 <= 3 && C.hv < 0.5f && g.nu >= 4) {
+                float F[4];
+                trap_cells4(C.T, d0, d1, F);
+                // 4-cell window [as, as + 3] inside the detector; shift the
+                // weights when the footprint sits on the last cells
+                const int a0 = C.aref + d0;
+                const int as = min(a0, g.nu - 4);
+                const int sh = a0 - as;  // 0..3
                 float Fu[4];
-                trap_cells4(C.T, d0, d1, Fu);
-                int ai[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) ai[q] = C.aref + (d0 + q <= d1 ? d0 + q : d0);
+                for (int q = 0; q < 4; ++q) {
+                    float w = 0.f;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) w = (q - sh == p) ? F[p] : w;
+                    Fu[q] = w;
+                }
                 // rows touched by the chunk, one guard row each side
                 const float fa = fmaf(C.sv, (float)kbeg, C.fv0), fb = fmaf(C.sv, (float)(kend - 1), C.fv0);
                 const int rb0 = (int)floorf(fminf(fa, fb) - C.hv + 0.5f) - 1;
                 const int nr = min(NR, (int)floorf(fmaxf(fa, fb) + C.hv + 0.5f) + 2 - rb0);
+                const TIn *ya = yv + as;
+#pragma unroll 4
                 for (int r = 0; r < nr; ++r) {
                     const int b = rb0 + r;
                     float R = 0.f;
                     if (b >= 0 && b < g.nv) {
-                        const TIn *row = yv + (size_t)b * g.nu;
-                        R = Fu[0] * ld(row, ai[0]);
-                        R = fmaf(Fu[1], ld(row, ai[1]), R);
-                        R = fmaf(Fu[2], ld(row, ai[2]), R);
-                        R = fmaf(Fu[3], ld(row, ai[3]), R);
+                        const TIn *row = ya + (size_t)b * g.nu;
+                        R = Fu[0] * ld(row, 0);
+                        R = fmaf(Fu[1], ld(row, 1), R);
+                        R = fmaf(Fu[2], ld(row, 2), R);
+                        R = fmaf(Fu[3], ld(row, 3), R);
                     }
                     Rs[r][tid] = R;
                 }
+                float fk = (float)kbeg;
 #pragma unroll
-                for (int kk = 0; kk < ZT; ++kk) {
-                    const int k = kbeg + kk;
-                    if (k < kend) {
-                        int bref;
-                        float vf;
-                        split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                        const float lo = vf - C.hv, hi = vf + C.hv;
-                        const int e0 = (int)floorf(lo + 0.5f);
-                        const float Fv0 = overlap(lo, hi, e0 - 0.5f, e0 + 0.5f);
-                        const float Fv1 = overlap(lo, hi, e0 + 0.5f, e0 + 1.5f);
+                for (int kk = 0; kk < ZT; ++kk, fk += 1.f) {
+                    if (kbeg + kk < kend) {
+                        int bref, e0;
+                        float vf, Fv0, Fv1;
+                        split_cell(fmaf(C.sv, fk, C.fv0), bref, vf);
+                        two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
                         const int r0 = min(max(bref + e0 - rb0, 0), nr - 2);
-                        const float wz = fmaf((float)k, g.dz, V.o[2]);
+                        const float wz = fmaf(fk, g.dz, V.o[2]);
                         acc[kk] = fmaf(sf_amp_fast(C.invm, C.rxy2, wz),
                                        fmaf(Fv0, Rs[r0][tid], Fv1 * Rs[r0 + 1][tid]), acc[kk]);
                     }
@@ -309,7 +318,7 @@ constexpr int kItems = 256;
 constexpr int kSlabSeg = 1024;
 
 template <int RPT> struct SfFwdSmem {
-    float Z[kItems][8 * RPT + 1];
+    float Z[8 * RPT][kItems];  // [row][item]: conflict-free in both stages
     float Fu[4][kItems];
     int a0[kItems];
     int L0[kSlabSeg], cnt[kSlabSeg], off[kSlabSeg + 1];
@@ -381,7 +390,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 for (int r = 0; r < 4; ++r) S.Fu[r][tid] = Fu[r];
                 S.a0[tid] = C.aref + d0;
 #pragma unroll
-                for (int r = 0; r < BV; ++r) S.Z[tid][r] = 0.f;
+                for (int r = 0; r < BV; ++r) S.Z[r][tid] = 0.f;
                 // voxels whose axial rectangle can meet a row of the tile
                 const float hw = 0.5f + C.hv + kSearchPad;
                 const float rsv = 1.f / C.sv;
@@ -389,18 +398,37 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 const float kb = ((float)(B0 + BV - 1) - C.fv0 + hw) * rsv;
                 const int k0 = max(0, (int)ceilf(fminf(ka, kb)));
                 const int k1 = min(g.nz - 1, (int)floorf(fmaxf(ka, kb)));
-                const size_t cidx = (size_t)j * g.nx + i, zs = (size_t)g.nx * g.ny;
-                for (int k = k0; k <= k1; ++k) {
-                    int bref;
-                    float vf;
-                    split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                    const float wz = fmaf((float)k, g.dz, V.o[2]);
-                    const float val = sf_amp_fast(C.invm, C.rxy2, wz) * ld(x, (size_t)k * zs + cidx);
-                    const int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
-                    for (int e = e0; e <= e1; ++e) {
-                        const int r = bref + e - B0;
-                        if (r >= 0 && r < BV)
-                            S.Z[tid][r] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[tid][r]);
+                const TIn *xc = x + (size_t)j * g.nx + i;
+                const size_t zs = (size_t)g.nx * g.ny;
+                if (C.hv < 0.5f) {
+                    // axial rectangle shorter than a row: at most two rows per voxel
+#pragma unroll 4
+                    for (int k = k0; k <= k1; ++k) {
+                        int bref;
+                        float vf;
+                        split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                        const float wz = fmaf((float)k, g.dz, V.o[2]);
+                        const float val = sf_amp_fast(C.invm, C.rxy2, wz) * ld(xc, (size_t)k * zs);
+                        int e0;
+                        float Fv0, Fv1;
+                        two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
+                        const int r0 = bref + e0 - B0;
+                        if (r0 >= 0 && r0 < BV) S.Z[r0][tid] = fmaf(Fv0, val, S.Z[r0][tid]);
+                        if (r0 + 1 >= 0 && r0 + 1 < BV) S.Z[r0 + 1][tid] = fmaf(Fv1, val, S.Z[r0 + 1][tid]);
+                    }
+                } else {
+                    for (int k = k0; k <= k1; ++k) {
+                        int bref;
+                        float vf;
+                        split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                        const float wz = fmaf((float)k, g.dz, V.o[2]);
+                        const float val = sf_amp_fast(C.invm, C.rxy2, wz) * ld(xc, (size_t)k * zs);
+                        const int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
+                        for (int e = e0; e <= e1; ++e) {
+                            const int r = bref + e - B0;
+                            if (r >= 0 && r < BV)
+                                S.Z[r][tid] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[r][tid]);
+                        }
                     }
                 }
             }
@@ -428,7 +456,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         if (d < 0 || d > 3) continue;
                         const float w = S.Fu[d][item];
 #pragma unroll
-                        for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[item][threadIdx.y + 8 * r], acc[r]);
+                        for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[threadIdx.y + 8 * r][item], acc[r]);
                     }
                 }
             }
