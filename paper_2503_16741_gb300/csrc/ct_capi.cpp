@@ -345,6 +345,7 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     case CT_DD: e = ctp::launch_dd(dir, g->grid, g->dev_views, in_t, in, out_t, out, batch, s); break;
     default: e = ctp::launch_sf(dir, g->grid, g->dev_views, in_t, in, out_t, out, batch, s); break;
     }
+    if (e == cudaErrorMemoryAllocation) return fail(CT_ERR_OOM, "workspace allocation failed");
     if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return CT_OK;
 }

@@ -133,6 +133,29 @@ __device__ __forceinline__ void split_cell(float f, int &ref, float &frac) {
     frac = f - r;
 }
 
+// DD path length of cell (a, b): slab width times |d| / |d_main| of the ray
+// from the source to the cell centre (d in world coordinates).
+template <bool CURVED>
+__device__ __forceinline__ float dd_len(const CtView &V, const CtGrid &g, int a, int b) {
+    const float Vb = g.dv * ((float)b - V.Cv);
+    float d2, dm;
+    const int m = V.main_y;
+    const float nm = m ? V.nn[1] : V.nn[0];
+    const float um = m ? V.eu[1] : V.eu[0];
+    const float vm = m ? V.ev[1] : V.ev[0];
+    if (CURVED) {
+        float sg, cg;
+        sincosf(((float)a - V.Cu) / V.Ku, &sg, &cg);
+        d2 = fmaf(V.D, V.D, Vb * Vb);
+        dm = fmaf(V.D, fmaf(cg, nm, sg * um), Vb * vm);
+    } else {
+        const float U = g.du * ((float)a - V.Cu);
+        d2 = fmaf(V.D, V.D, fmaf(U, U, Vb * Vb));
+        dm = fmaf(V.D, nm, fmaf(U, um, Vb * vm));
+    }
+    return (m ? g.dy : g.dx) * sqrtf(d2) / fabsf(dm);
+}
+
 // ---------------------------------------------------------------- forward search
 // Candidate lateral/axial index box of slab s for the detector window
 // fu in [Flo, Fhi], fv in [Glo, Ghi] of a flat detector: the window's four

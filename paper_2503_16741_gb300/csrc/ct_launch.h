@@ -12,9 +12,17 @@ cudaError_t launch_sf(int dir, const CtGrid &g, const CtView *views, int in_t, c
                       int out_t, void *out, int batch, cudaStream_t st);
 cudaError_t launch_dd(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st);
+cudaError_t launch_dd_nc(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                         int out_t, void *out, int batch, cudaStream_t st);
 cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                          int out_t, void *out, int batch, cudaStream_t st);
 cudaError_t launch_ray(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                        int out_t, void *out, int batch, cudaStream_t st);
+
+// Stream-ordered scratch from a library-owned pool on the current device
+// (memory is kept in the pool between calls, so steady-state calls do not
+// reach the driver's allocator).
+cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t st);
+cudaError_t workspace_free(void *p, cudaStream_t st);
 
 }  // namespace ctp

@@ -1,5 +1,6 @@
 // k_dd.cu -- distance-driven projector (De Man & Basu 2004, cited in Sec.
-// 2.3).  Per view the slabs run along the main axis (x or y, whichever the
+// 2.3) in non-circular geometry (the circular kernels share the footprint
+// kernels of k_sf.cu).  Per view the slabs run along the main axis (x or y, whichever the
 // central ray follows more closely).  A voxel's transaxial boundary points
 // (+- half a voxel along the other axis) and axial boundary points
 // (+- dz/2) are projected to the detector; the weight of cell (a, b) is
@@ -13,57 +14,6 @@ namespace ctp {
 
 __device__ __forceinline__ float dd_ratio(float K, float c, float b, float dc, float db) {
     return K * fmaf(dc, b, -c * db) / ((b + db) * b);
-}
-
-// L_c of cell (a, b): slab width times |d| / |d_main| of the ray from the
-// source to the cell centre, d in world coordinates.
-template <bool CURVED>
-__device__ __forceinline__ float dd_len(const CtView &V, const CtGrid &g, int a, int b) {
-    const float Vb = g.dv * ((float)b - V.Cv);
-    float d2, dm;
-    const int m = V.main_y;
-    const float nm = m ? V.nn[1] : V.nn[0];
-    const float um = m ? V.eu[1] : V.eu[0];
-    const float vm = m ? V.ev[1] : V.ev[0];
-    if (CURVED) {
-        float sg, cg;
-        sincosf(((float)a - V.Cu) / V.Ku, &sg, &cg);
-        d2 = fmaf(V.D, V.D, Vb * Vb);
-        dm = fmaf(V.D, fmaf(cg, nm, sg * um), Vb * vm);
-    } else {
-        const float U = g.du * ((float)a - V.Cu);
-        d2 = fmaf(V.D, V.D, fmaf(U, U, Vb * Vb));
-        dm = fmaf(V.D, nm, fmaf(U, um, Vb * vm));
-    }
-    return (m ? g.dy : g.dx) * sqrtf(d2) / fabsf(dm);
-}
-
-// circular geometry: transaxial boundaries do not depend on z
-struct DdCol {
-    int aref;
-    float ulo, uhi;   // boundary projections relative to cell aref
-    float sv, fv0, hv;
-};
-
-template <bool CURVED>
-__device__ __forceinline__ DdCol dd_col(const CtView &V, int i, int j) {
-    const float fi = (float)i, fj = (float)j;
-    const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
-    const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, V.an[3]));
-    DdCol C;
-    float fr;
-    split_cell(Det<CURVED>::fu(V, cu, cn), C.aref, fr);
-    const int q = V.main_y ? 0 : 1;  // boundary offset along the non-main axis
-    const float hu = 0.5f * V.au[q], hn = 0.5f * V.an[q];
-    const float e1 = fr + Det<CURVED>::dfu(V, cu, cn, -hu, -hn);
-    const float e2 = fr + Det<CURVED>::dfu(V, cu, cn, hu, hn);
-    C.ulo = fminf(e1, e2);
-    C.uhi = fmaxf(e1, e2);
-    const float den = Det<CURVED>::den(cu, cn);
-    C.sv = V.Kv * V.av[2] / den;
-    C.fv0 = fmaf(V.Kv, V.av[3] / den, V.Cv);
-    C.hv = 0.5f * fabsf(C.sv);
-    return C;
 }
 
 struct DdVox {
@@ -95,69 +45,6 @@ __device__ __forceinline__ DdVox dd_vox_nc(const CtView &V, int i, int j, int k)
 }
 
 // ------------------------------------------------------------ back (gather)
-template <typename TIn, bool CURVED, int ZT>
-__global__ void __launch_bounds__(128)
-dd_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
-             void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
-    int bx = blockIdx.x;
-    const int tx = bx % tiles_x; bx /= tiles_x;
-    const int kc = bx % nzc;
-    const int bt = bx / nzc;
-    const int i = tx * 32 + threadIdx.x;
-    const int j = blockIdx.y * 4 + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const int kbeg = kc * ZT;
-    float acc[ZT];
-#pragma unroll
-    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
-    const size_t vstride = (size_t)g.nv * g.nu;
-    const TIn *ys = sino + (size_t)bt * g.nview * vstride;
-    for (int v = 0; v < g.nview; ++v) {
-        const CtView &V = views[v];
-        const DdCol C = dd_col<CURVED>(V, i, j);
-        int d0 = (int)floorf(C.ulo + 0.5f), d1 = (int)floorf(C.uhi + 0.5f);
-        d0 = max(d0, -C.aref);
-        d1 = min(d1, g.nu - 1 - C.aref);
-        const TIn *yv = ys + (size_t)v * vstride;
-        for (int db = d0; db <= d1; db += 4) {
-            float Ou[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                Ou[q] = (db + q <= d1) ? overlap(C.ulo, C.uhi, db + q - 0.5f, db + q + 0.5f) : 0.f;
-            const int abase = C.aref + db;
-            const int na = min(4, d1 - db + 1);
-#pragma unroll
-            for (int kk = 0; kk < ZT; ++kk) {
-                const int k = kbeg + kk;
-                if (k >= g.nz) break;
-                int bref;
-                float vf;
-                split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
-                e0 = max(e0, -bref);
-                e1 = min(e1, g.nv - 1 - bref);
-                float s = 0.f;
-                for (int e = e0; e <= e1; ++e) {
-                    const int b = bref + e;
-                    const float Ov = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
-                    const TIn *row = yv + (size_t)b * g.nu + abase;
-                    float r = Ou[0] * dd_len<CURVED>(V, g, abase, b) * ld(row, 0);
-                    for (int q = 1; q < na; ++q)
-                        r = fmaf(Ou[q] * dd_len<CURVED>(V, g, abase + q, b), ld(row, q), r);
-                    s = fmaf(Ov, r, s);
-                }
-                acc[kk] += s;
-            }
-        }
-    }
-    const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
-#pragma unroll
-    for (int kk = 0; kk < ZT; ++kk) {
-        const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
-    }
-}
-
 template <typename TIn, int ZT>
 __global__ void __launch_bounds__(128)
 dd_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
@@ -213,49 +100,6 @@ dd_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 }
 
 // ------------------------------------------------------------ forward (gather)
-template <typename TIn, bool CURVED>
-__global__ void __launch_bounds__(256)
-dd_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
-            void *__restrict__ sino, int out_t, int tiles_u) {
-    int bx = blockIdx.x;
-    const int tu = bx % tiles_u; bx /= tiles_u;
-    const int v = bx % g.nview;
-    const int bt = bx / g.nview;
-    const int a = tu * 32 + threadIdx.x;
-    const int b = blockIdx.y * 8 + threadIdx.y;
-    if (a >= g.nu || b >= g.nv) return;
-    const CtView &V = views[v];
-    const int main_y = V.main_y;
-    const SlabCoef sc = slab_coef(V, main_y);
-    const float mu = V.m_dd_u + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
-    const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
-    const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
-    float acc = 0.f;
-    for (int s = 0; s < nslab; ++s) {
-        int l0, l1, k0, k1;
-        if (!slab_search<CURVED>(V, sc, s, a - mu, a + mu, b - mv, b + mv, nlat, g.nz, l0, l1, k0, k1))
-            continue;
-        for (int l = l0; l <= l1; ++l) {
-            const int i = main_y ? l : s, j = main_y ? s : l;
-            const DdCol C = dd_col<CURVED>(V, i, j);
-            const int d = a - C.aref;
-            const float Ou = overlap(C.ulo, C.uhi, d - 0.5f, d + 0.5f);
-            if (Ou == 0.f) continue;
-            for (int k = k0; k <= k1; ++k) {
-                int bref;
-                float vf;
-                split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                const int e = b - bref;
-                const float Ov = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
-                if (Ov == 0.f) continue;
-                acc = fmaf(Ou * Ov, ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
-            }
-        }
-    }
-    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc * dd_len<CURVED>(V, g, a, b),
-       out_t);
-}
-
 template <typename TIn>
 __global__ void __launch_bounds__(256)
 dd_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
@@ -297,38 +141,28 @@ namespace {
 constexpr int kZT = 8;
 
 template <typename TIn>
-cudaError_t dd_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
-                        int out_t, int batch, cudaStream_t st) {
+cudaError_t dd_nc_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
+                           int out_t, int batch, cudaStream_t st) {
     const TIn *src = static_cast<const TIn *>(in);
     if (dir == 0) {
         const int tiles_u = (g.nu + 31) / 32;
         dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
-        if (g.variant == GEO_NONCIRC_FLAT)
-            dd_fwd_nc<TIn><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-        else if (g.variant == GEO_CIRC_CURVED)
-            dd_fwd_circ<TIn, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-        else
-            dd_fwd_circ<TIn, false><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        dd_fwd_nc<TIn><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
     } else {
         const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
         dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-        if (g.variant == GEO_NONCIRC_FLAT)
-            dd_back_nc<TIn, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
-        else if (g.variant == GEO_CIRC_CURVED)
-            dd_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
-        else
-            dd_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        dd_back_nc<TIn, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     }
     return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_dd(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
-                      int out_t, void *out, int batch, cudaStream_t st) {
+cudaError_t launch_dd_nc(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                         int out_t, void *out, int batch, cudaStream_t st) {
     switch (in_t) {
-    case 0: return dd_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
-    case 1: return dd_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
-    default: return dd_launch_t<__nv_bfloat16>(dir, g, views, in, out, out_t, batch, st);
+    case 0: return dd_nc_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
+    case 1: return dd_nc_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
+    default: return dd_nc_launch_t<__nv_bfloat16>(dir, g, views, in, out, out_t, batch, st);
     }
 }
 

@@ -1,9 +1,19 @@
-// k_sf.cu -- separable-footprint projector SF-TR (Long, Fessler & Balter
-// 2010, cited in Sec. 2.3): trapezoid transaxial footprint from the four
-// projected column corners, rectangle axial footprint from the projected
-// end points, amplitude dx / max(|cos|, |sin|) of the 3D ray to the voxel
-// centre.  Forward and back are gather kernels (no atomics) that evaluate the
-// same per-voxel weight functions, so they form a matched pair.
+// k_sf.cu -- footprint projectors in circular geometry, and the SF-TR
+// projector in non-circular geometry.
+// SF-TR (Long, Fessler & Balter 2010, cited in Sec. 2.3): trapezoid
+// transaxial footprint from the four projected column corners, rectangle
+// axial footprint from the projected end points, amplitude dx / max(|cos|,
+// |sin|) of the 3D ray to the voxel centre.
+// DD (De Man & Basu 2004, cited in Sec. 2.3) in circular geometry shares the
+// kernels: its transaxial footprint is the box between the two projected
+// boundary points (a trapezoid with vertical sides), its axial footprint the
+// same rectangle, its amplitude 1, and each cell carries the path length L_c
+// of its central ray through one slab -- applied once per cell after the
+// gather in the forward, and to the sinogram before the gather in the back.
+// Forward and back are gather kernels (no atomics) that evaluate the same
+// per-voxel weight functions, so they form a matched pair.
+#include <algorithm>
+
 #include "ct_device.cuh"
 #include "ct_launch.h"
 
@@ -21,7 +31,7 @@ struct SfCol {
     float rxy2;    // w_x^2 + w_y^2
 };
 
-template <bool CURVED>
+template <bool CURVED, bool DD = false>
 __device__ __forceinline__ SfCol sf_col(const CtView &V, const CtGrid &g, int i, int j) {
     const float fi = (float)i, fj = (float)j;
     const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
@@ -29,14 +39,24 @@ __device__ __forceinline__ SfCol sf_col(const CtView &V, const CtGrid &g, int i,
     SfCol C;
     float fr;
     split_cell(Det<CURVED>::fu(V, cu, cn), C.aref, fr);
-    const float hxu = 0.5f * V.au[0], hxn = 0.5f * V.an[0];
-    const float hyu = 0.5f * V.au[1], hyn = 0.5f * V.an[1];
-    float t0 = fr + Det<CURVED>::dfu(V, cu, cn, -hxu - hyu, -hxn - hyn);
-    float t1 = fr + Det<CURVED>::dfu(V, cu, cn, hxu - hyu, hxn - hyn);
-    float t2 = fr + Det<CURVED>::dfu(V, cu, cn, -hxu + hyu, -hxn + hyn);
-    float t3 = fr + Det<CURVED>::dfu(V, cu, cn, hxu + hyu, hxn + hyn);
-    sort4(t0, t1, t2, t3);
-    C.T = make_trap(t0, t1, t2, t3);
+    if (DD) {
+        // boundary points +- half a voxel along the non-main axis
+        const int q = V.main_y ? 0 : 1;
+        const float hu = 0.5f * V.au[q], hn = 0.5f * V.an[q];
+        const float e1 = fr + Det<CURVED>::dfu(V, cu, cn, -hu, -hn);
+        const float e2 = fr + Det<CURVED>::dfu(V, cu, cn, hu, hn);
+        const float lo = fminf(e1, e2), hi = fmaxf(e1, e2);
+        C.T = make_trap(lo, lo, hi, hi);
+    } else {
+        const float hxu = 0.5f * V.au[0], hxn = 0.5f * V.an[0];
+        const float hyu = 0.5f * V.au[1], hyn = 0.5f * V.an[1];
+        float t0 = fr + Det<CURVED>::dfu(V, cu, cn, -hxu - hyu, -hxn - hyn);
+        float t1 = fr + Det<CURVED>::dfu(V, cu, cn, hxu - hyu, hxn - hyn);
+        float t2 = fr + Det<CURVED>::dfu(V, cu, cn, -hxu + hyu, -hxn + hyn);
+        float t3 = fr + Det<CURVED>::dfu(V, cu, cn, hxu + hyu, hxn + hyn);
+        sort4(t0, t1, t2, t3);
+        C.T = make_trap(t0, t1, t2, t3);
+    }
     const float kd = V.Kv / Det<CURVED>::den(cu, cn);
     C.sv = kd * V.av[2];
     C.fv0 = fmaf(kd, V.av[3], V.Cv);
@@ -115,8 +135,13 @@ __device__ __forceinline__ float sf_amp_fast(float invm, float rxy2, float wz) {
     const float t = fmaf(wz, wz, rxy2);
     return invm * t * rsqrtf(t);
 }
+// per-voxel amplitude: SF as above, DD 1 (its factor is per cell)
+template <bool DD, typename C_>
+__device__ __forceinline__ float fp_amp(const C_ &C, float wz) {
+    return DD ? 1.f : sf_amp_fast(C.invm, C.rxy2, wz);
+}
 
-template <typename TIn, bool CURVED, int ZT>
+template <typename TIn, bool CURVED, bool DD, int ZT>
 __global__ void __launch_bounds__(128, 7)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
@@ -150,7 +175,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
         if (!active) continue;
         for (int vv = 0; vv < nvc; ++vv) {
             const CtView &V = sview[vv];
-            const SfCol C = sf_col<CURVED>(V, g, i, j);
+            const SfCol C = sf_col<CURVED, DD>(V, g, i, j);
             int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
             d0 = max(d0, -C.aref);
             d1 = min(d1, g.nu - 1 - C.aref);
@@ -200,8 +225,8 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                         two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
                         const int r0 = min(max(bref + e0 - rb0, 0), nr - 2);
                         const float wz = fmaf(fk, g.dz, V.o[2]);
-                        acc[kk] = fmaf(sf_amp_fast(C.invm, C.rxy2, wz),
-                                       fmaf(Fv0, Rs[r0][tid], Fv1 * Rs[r0 + 1][tid]), acc[kk]);
+                        acc[kk] = fmaf(fp_amp<DD>(C, wz), fmaf(Fv0, Rs[r0][tid], Fv1 * Rs[r0 + 1][tid]),
+                                       acc[kk]);
                     }
                 }
                 continue;
@@ -231,7 +256,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                         s = fmaf(Fv, r, s);
                     }
                     const float wz = fmaf((float)k, g.dz, V.o[2]);
-                    Gs[kk][tid] = fmaf(sf_amp_fast(C.invm, C.rxy2, wz), s, Gs[kk][tid]);
+                    Gs[kk][tid] = fmaf(fp_amp<DD>(C, wz), s, Gs[kk][tid]);
                 }
             }
         }
@@ -324,7 +349,7 @@ template <int RPT> struct SfFwdSmem {
     int L0[kSlabSeg], cnt[kSlabSeg], off[kSlabSeg + 1];
 };
 
-template <typename TIn, bool CURVED, int RPT>
+template <typename TIn, bool CURVED, bool DD, int RPT>
 __global__ void __launch_bounds__(256, 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
             void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
@@ -342,7 +367,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
     const CtView &V = views[v];
     const int main_y = V.main_y;
     const SlabCoef sc = slab_coef(V, main_y);
-    const float mu = V.m_sf_u + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
+    const float mu = (DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
     const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
     const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
     const float T1 = Det<CURVED>::ratio_at(V, a - mu), T2 = Det<CURVED>::ratio_at(V, a + mu);
@@ -382,7 +407,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 const int s = seg + lo;
                 const int l = S.L0[lo] + (q - S.off[lo]);
                 const int i = main_y ? l : s, j = main_y ? s : l;
-                const SfCol C = sf_col<CURVED>(V, g, i, j);
+                const SfCol C = sf_col<CURVED, DD>(V, g, i, j);
                 int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
                 float Fu[4];
                 trap_cells4(C.T, d0, d1, Fu);
@@ -408,7 +433,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         float vf;
                         split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
                         const float wz = fmaf((float)k, g.dz, V.o[2]);
-                        const float val = sf_amp_fast(C.invm, C.rxy2, wz) * ld(xc, (size_t)k * zs);
+                        const float val = fp_amp<DD>(C, wz) * ld(xc, (size_t)k * zs);
                         int e0;
                         float Fv0, Fv1;
                         two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
@@ -422,7 +447,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         float vf;
                         split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
                         const float wz = fmaf((float)k, g.dz, V.o[2]);
-                        const float val = sf_amp_fast(C.invm, C.rxy2, wz) * ld(xc, (size_t)k * zs);
+                        const float val = fp_amp<DD>(C, wz) * ld(xc, (size_t)k * zs);
                         const int e0 = (int)floorf(vf - C.hv + 0.5f), e1 = (int)floorf(vf + C.hv + 0.5f);
                         for (int e = e0; e <= e1; ++e) {
                             const int r = bref + e - B0;
@@ -467,7 +492,9 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int b = B0 + threadIdx.y + 8 * r;
-            if (b < g.nv) st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc[r], out_t);
+            if (b < g.nv)
+                st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
+                   DD ? acc[r] * dd_len<CURVED>(V, g, a, b) : acc[r], out_t);
         }
     }
 }
@@ -482,7 +509,7 @@ struct SfColS {
 };
 constexpr int kCols = 256;
 
-template <typename TIn, bool CURVED>
+template <typename TIn, bool CURVED, bool DD>
 __global__ void __launch_bounds__(256)
 sf_fwd_circ_wide(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
                  void *__restrict__ sino, int out_t, int tiles_u) {
@@ -498,7 +525,7 @@ sf_fwd_circ_wide(CtGrid g, const CtView *__restrict__ views, const TIn *__restri
     const CtView &V = views[v];
     const int main_y = V.main_y;
     const SlabCoef sc = slab_coef(V, main_y);
-    const float mu = V.m_sf_u + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
+    const float mu = (DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
     const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
     const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
     const float T1 = Det<CURVED>::ratio_at(V, a - mu), T2 = Det<CURVED>::ratio_at(V, a + mu);
@@ -519,7 +546,7 @@ sf_fwd_circ_wide(CtGrid g, const CtView *__restrict__ views, const TIn *__restri
             __syncthreads();
             for (int t = tid; t < nc; t += 256) {
                 const int l = cb + t;
-                const SfCol C = sf_col<CURVED>(V, g, main_y ? l : s, main_y ? s : l);
+                const SfCol C = sf_col<CURVED, DD>(V, g, main_y ? l : s, main_y ? s : l);
                 SfColS &Q = cols[t];
                 Q.T = C.T; Q.aref = C.aref; Q.sv = C.sv; Q.fv0 = C.fv0; Q.hv = C.hv;
                 Q.invm = C.invm; Q.rxy2 = C.rxy2; Q.rsv = 1.f / C.sv;
@@ -544,13 +571,15 @@ sf_fwd_circ_wide(CtGrid g, const CtView *__restrict__ views, const TIn *__restri
                     const float Fv = overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f);
                     if (Fv == 0.f) continue;
                     const float wz = fmaf((float)k, g.dz, V.o[2]);
-                    acc = fmaf(sf_amp_fast(C.invm, C.rxy2, wz) * Fu * Fv,
+                    acc = fmaf(fp_amp<DD>(C, wz) * Fu * Fv,
                                ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
                 }
             }
         }
     }
-    if (active) st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+    if (active)
+        st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
+           DD ? acc * dd_len<CURVED>(V, g, a, b) : acc, out_t);
 }
 
 template <typename TIn>
@@ -590,20 +619,63 @@ sf_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vo
     st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
 }
 
+// ------------------------------------------------------------ DD cell factor
+// y'[b][a] = L_c(a, b) y[b][a] for every view: the per-cell path length of
+// the DD weight, applied before the back gather (which then has amplitude 1).
+template <typename TIn, bool CURVED>
+__global__ void __launch_bounds__(256)
+dd_prescale(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ y,
+            float *__restrict__ yp, int batch) {
+    const size_t nview_cells = (size_t)g.nv * g.nu;
+    const size_t total = nview_cells * g.nview * batch;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t % g.nu);
+        const int b = (int)((t / g.nu) % g.nv);
+        const int v = (int)((t / nview_cells) % g.nview);
+        yp[t] = dd_len<CURVED>(views[v], g, a, b) * ld(y, t);
+    }
+}
+
 // ------------------------------------------------------------ launchers
 namespace {
 constexpr int kZT = 16;
 
-template <typename TIn, bool CURVED, int RPT>
-cudaError_t sf_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
+template <typename TIn, bool CURVED, bool DD, int RPT>
+cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                           int batch, cudaStream_t st) {
     const int tiles_u = (g.nu + 31) / 32, tiles_v = (g.nv + 8 * RPT - 1) / (8 * RPT);
     const size_t smem = sizeof(SfFwdSmem<RPT>);
-    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, RPT>,
+    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 blk(32, 8), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
-    sf_fwd_circ<TIn, CURVED, RPT><<<grd, blk, smem, st>>>(g, views, src, out, out_t, tiles_u, tiles_v);
+    sf_fwd_circ<TIn, CURVED, DD, RPT><<<grd, blk, smem, st>>>(g, views, src, out, out_t, tiles_u, tiles_v);
+    return cudaGetLastError();
+}
+
+// forward, circular geometry
+template <typename TIn, bool CURVED, bool DD>
+cudaError_t fp_fwd_circ(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
+                        int batch, cudaStream_t st) {
+    // every transaxial footprint spans at most 4 cells when its half width
+    // (bounded per view on the host) is at most 1.5 cells
+    if ((DD ? g.max_m_dd_u : g.max_m_sf_u) <= 1.5f) {
+        if (g.nv >= 64) return fp_fwd_stream<TIn, CURVED, DD, 8>(g, views, src, out, out_t, batch, st);
+        return fp_fwd_stream<TIn, CURVED, DD, 1>(g, views, src, out, out_t, batch, st);
+    }
+    const int tiles_u = (g.nu + 31) / 32;
+    dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
+    sf_fwd_circ_wide<TIn, CURVED, DD><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+    return cudaGetLastError();
+}
+
+template <typename TIn, bool CURVED, bool DD>
+cudaError_t fp_back_circ(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
+                         int batch, cudaStream_t st) {
+    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+    dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+    sf_back_circ<TIn, CURVED, DD, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     return cudaGetLastError();
 }
 
@@ -611,41 +683,52 @@ template <typename TIn>
 cudaError_t sf_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
                         int out_t, int batch, cudaStream_t st) {
     const TIn *src = static_cast<const TIn *>(in);
+    const bool curved = g.variant == GEO_CIRC_CURVED;
     if (dir == 0) {
-        const int tiles_u = (g.nu + 31) / 32;
         if (g.variant == GEO_NONCIRC_FLAT) {
+            const int tiles_u = (g.nu + 31) / 32;
             dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
             sf_fwd_nc<TIn><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
             return cudaGetLastError();
         }
-        // every transaxial footprint spans at most 4 cells when its half
-        // width (bounded per view) is at most 1.5 cells
-        if (g.max_m_sf_u <= 1.5f) {
-            const bool curved = g.variant == GEO_CIRC_CURVED;
-            if (g.nv >= 64)
-                return curved ? sf_fwd_stream<TIn, true, 8>(g, views, src, out, out_t, batch, st)
-                              : sf_fwd_stream<TIn, false, 8>(g, views, src, out, out_t, batch, st);
-            return curved ? sf_fwd_stream<TIn, true, 1>(g, views, src, out, out_t, batch, st)
-                          : sf_fwd_stream<TIn, false, 1>(g, views, src, out, out_t, batch, st);
-        }
-        dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
-        if (g.variant == GEO_CIRC_CURVED)
-            sf_fwd_circ_wide<TIn, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-        else
-            sf_fwd_circ_wide<TIn, false><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        return curved ? fp_fwd_circ<TIn, true, false>(g, views, src, out, out_t, batch, st)
+                      : fp_fwd_circ<TIn, false, false>(g, views, src, out, out_t, batch, st);
+    }
+    if (g.variant == GEO_NONCIRC_FLAT) {
+        const int tiles_x = (g.nx + 31) / 32, nzc8 = (g.nz + 7) / 8;
+        dim3 blk(32, 4), grd8((unsigned)(tiles_x * nzc8 * batch), (unsigned)((g.ny + 3) / 4));
+        sf_back_nc<TIn, 8><<<grd8, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc8);
         return cudaGetLastError();
     }
-    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
-    dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-    if (g.variant == GEO_NONCIRC_FLAT) {
-        const int nzc8 = (g.nz + 7) / 8;
-        dim3 grd8((unsigned)(tiles_x * nzc8 * batch), (unsigned)((g.ny + 3) / 4));
-        sf_back_nc<TIn, 8><<<grd8, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc8);
-    } else if (g.variant == GEO_CIRC_CURVED)
-        sf_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    return curved ? fp_back_circ<TIn, true, false>(g, views, src, out, out_t, batch, st)
+                  : fp_back_circ<TIn, false, false>(g, views, src, out, out_t, batch, st);
+}
+
+// DD in circular geometry; the back direction scales the sinogram by L_c
+// into a stream-ordered FP32 workspace first
+template <typename TIn>
+cudaError_t dd_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
+                        int out_t, int batch, cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    const bool curved = g.variant == GEO_CIRC_CURVED;
+    if (dir == 0)
+        return curved ? fp_fwd_circ<TIn, true, true>(g, views, src, out, out_t, batch, st)
+                      : fp_fwd_circ<TIn, false, true>(g, views, src, out, out_t, batch, st);
+    const size_t n = (size_t)g.nview * g.nv * g.nu * batch;
+    float *yp = nullptr;
+    cudaError_t e = workspace_alloc((void **)&yp, n * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152u * 64u);
+    if (curved)
+        dd_prescale<TIn, true><<<blocks, 256, 0, st>>>(g, views, src, yp, batch);
     else
-        sf_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
-    return cudaGetLastError();
+        dd_prescale<TIn, false><<<blocks, 256, 0, st>>>(g, views, src, yp, batch);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = curved ? fp_back_circ<float, true, true>(g, views, yp, out, out_t, batch, st)
+                   : fp_back_circ<float, false, true>(g, views, yp, out, out_t, batch, st);
+    const cudaError_t ef = workspace_free(yp, st);
+    return e != cudaSuccess ? e : ef;
 }
 }  // namespace
 
@@ -655,6 +738,16 @@ cudaError_t launch_sf(int dir, const CtGrid &g, const CtView *views, int in_t, c
     case 0: return sf_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
     case 1: return sf_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
     default: return sf_launch_t<__nv_bfloat16>(dir, g, views, in, out, out_t, batch, st);
+    }
+}
+
+cudaError_t launch_dd(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                      int out_t, void *out, int batch, cudaStream_t st) {
+    if (g.variant == GEO_NONCIRC_FLAT) return launch_dd_nc(dir, g, views, in_t, in, out_t, out, batch, st);
+    switch (in_t) {
+    case 0: return dd_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
+    case 1: return dd_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
+    default: return dd_launch_t<__nv_bfloat16>(dir, g, views, in, out, out_t, batch, st);
     }
 }
 

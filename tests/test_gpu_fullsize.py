@@ -1,0 +1,76 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configuration the benchmark times, on outputs the oracle can afford: the
+forward projection of a few views (a view subset is a geometry of its own)
+and the backprojection at sampled voxels (all views)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import workloads as W
+from gpu_util import TOL_F16, TOL_F32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ct():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_16741_gb300 as ct
+    ct.load()
+    return ct
+
+
+def _sample_voxels(spec, n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.choice(spec.n_vox, size=n, replace=False)
+
+
+@pytest.mark.parametrize("proj", ["sf", "dd"])
+def test_circ3d_256_full_size(ct, proj):
+    spec = W.circ3d_256()
+    x = W.phantom(spec, seed=0)
+    g = ct.Geometry.from_spec(spec)
+    xd = torch.as_tensor(x, dtype=torch.float32).cuda()
+    y = ct.forward(g, xd, proj)
+    xb = ct.back(g, y, proj)
+    torch.cuda.synchronize()
+    views = [0, 47, 133, 271]
+    y_ref = oracle.forward(spec.subset(views), proj, x)
+    assert rel_l2(y[views].cpu().numpy(), y_ref) <= TOL_F32
+    sel = _sample_voxels(spec, 300, 1)
+    xb_ref = oracle.back_voxels(spec, proj, y.double().cpu().numpy(), sel)
+    assert rel_l2(xb.cpu().numpy().ravel()[sel], xb_ref) <= TOL_F32
+
+
+def test_circ3d_curved_full_size_dd(ct):
+    spec = W.circ3d_curved()
+    x = W.phantom(spec, seed=2)
+    g = ct.Geometry.from_spec(spec)
+    y = ct.forward(g, torch.as_tensor(x, dtype=torch.float32).cuda(), "dd")
+    torch.cuda.synchronize()
+    views = [5, 500]
+    assert rel_l2(y[views].cpu().numpy(), oracle.forward(spec.subset(views), "dd", x)) <= TOL_F32
+    s = W.random_sino(spec, seed=2)[0].astype(np.float32)
+    xb = ct.back(g, torch.as_tensor(s).cuda(), "dd")
+    sel = _sample_voxels(spec, 200, 2)
+    ref = oracle.back_voxels(spec, "dd", s.astype(np.float64), sel)
+    assert rel_l2(xb.cpu().numpy().ravel()[sel], ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("dtype,bound", [(torch.float32, TOL_F32), (torch.float16, TOL_F16)])
+def test_noncirc_512_full_size_sf(ct, dtype, bound):
+    spec = W.noncirc3d_saddle()
+    x = W.phantom(spec, seed=0)
+    g = ct.Geometry.from_spec(spec)
+    y = ct.forward(g, torch.as_tensor(x, dtype=dtype).cuda(), "sf")
+    torch.cuda.synchronize()
+    views = [123]
+    assert rel_l2(y[views].float().cpu().numpy(), oracle.forward(spec.subset(views), "sf", x)) <= bound
+    sel = _sample_voxels(spec, 100, 3)
+    yy = y.float()
+    xb = ct.back(g, y, "sf")
+    ref = oracle.back_voxels(spec, "sf", yy.double().cpu().numpy(), sel)
+    assert rel_l2(xb.float().cpu().numpy().ravel()[sel], ref) <= bound
