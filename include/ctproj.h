@@ -153,6 +153,31 @@ ct_status ct_back(const ct_geometry *geom, ct_projector proj, ct_mode mode,
                   ct_dtype in_t, const void *sino, ct_dtype out_t, void *vol,
                   int batch, void *cuda_stream);
 
+/* Distance-driven backprojection (as ct_back with CT_DD, CT_MODE_PROJ) that
+ * allocates no device memory.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc or take memory from a pool
+ * -- a service whose device memory is owned and accounted for by another
+ * allocator, a plug-in inside a host application that forbids allocation
+ * after start-up, or a latency-critical path that must not risk an
+ * allocation.  ct_back's DD path needs a scratch copy of the sinogram scaled
+ * by each cell's path length; here that scratch is a fixed device array of
+ * 16,777,216 floats (64 MiB) compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   geom:  a fan-beam or circular geometry (non-circular DD backprojection
+ *          needs no scratch: use ct_back; CT_ERR_UNSUPPORTED here);
+ *   sino, vol, in_t, out_t, batch, cuda_stream: as for ct_back; the caller
+ *          owns both buffers.
+ * Limit: batch x nview x nv x nu <= 16,777,216, else CT_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address once (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the one array: calls whose work overlaps on
+ * the GPU (on different streams, or from different threads) race and give
+ * wrong results -- serialise them.  The array keeps the previous call's
+ * contents; nothing in it needs to start at zero, since each call writes
+ * every element it reads.  Results equal ct_back with CT_DD bit for bit. */
+ct_status ct_back_dd_noalloc(const ct_geometry *geom, ct_dtype in_t, const void *sino,
+                             ct_dtype out_t, void *vol, int batch, void *cuda_stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *ct_last_error(void);
 

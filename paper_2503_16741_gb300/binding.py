@@ -83,6 +83,9 @@ def load():
         sig = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
         lib.ct_forward.argtypes = sig
         lib.ct_back.argtypes = sig
+        lib.ct_back_dd_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                           C.c_int, C.c_void_p]
+        lib.ct_back_dd_noalloc.restype = C.c_int
         lib.ct_last_error.restype = C.c_char_p
         lib.ct_version.restype = C.c_char_p
         for f in ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_shape", "ct_forward", "ct_back"):
@@ -237,3 +240,17 @@ def back(geom: Geometry, y: torch.Tensor, projector: str = "sf", mode: str = "pr
     lead = y.shape[:-len(geom.sino_shape)]
     x = torch.empty(tuple(lead) + geom.vol_shape, dtype=out_dtype or y.dtype, device=y.device)
     return back_into(geom, y, x, projector, mode, stream)
+
+
+def back_dd_noalloc(geom: Geometry, y: torch.Tensor, out_dtype: Optional[torch.dtype] = None,
+                    stream=None) -> torch.Tensor:
+    """DD backprojection through ct_back_dd_noalloc: the library allocates
+    nothing (its scratch is a fixed device array); the output tensor is
+    allocated here by PyTorch."""
+    _check_tensor(y, "sinogram")
+    b = _batch_of(y, geom.sino_shape, "sinogram")
+    lead = y.shape[:-len(geom.sino_shape)]
+    x = torch.empty(tuple(lead) + geom.vol_shape, dtype=out_dtype or y.dtype, device=y.device)
+    _check(load().ct_back_dd_noalloc(geom.handle, DTYPES[y.dtype], y.data_ptr(), DTYPES[x.dtype],
+                                     x.data_ptr(), b, _stream_ptr(stream)))
+    return x

@@ -12,21 +12,13 @@
 #include <vector>
 
 #include "../../include/ctproj.h"
+#include "ct_geometry.h"
 #include "ct_launch.h"
 #include "ct_types.h"
 
 using ctp::CtGrid;
 using ctp::CtView;
 
-struct ct_geometry {
-    int kind = 0, det = 0;
-    int nx = 0, ny = 0, nz = 0, nu = 0, nv = 0, nview = 0;
-    double dx = 0, dy = 0, dz = 0, du = 0, dv = 0;
-    CtGrid grid{};
-    std::vector<CtView> host_views;
-    CtView *dev_views = nullptr;
-    int device = -1;
-};
 
 namespace {
 
@@ -109,6 +101,8 @@ void view_pose(const ct_geometry_desc *d, int v, const Param P[], Vec3 &s, Vec3 
 }
 
 }  // namespace
+
+void ctp::set_last_error(const std::string &msg) { g_err = msg; }
 
 extern "C" {
 

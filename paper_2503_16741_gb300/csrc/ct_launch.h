@@ -19,6 +19,9 @@ cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t
 cudaError_t launch_ray(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                        int out_t, void *out, int batch, cudaStream_t st);
 
+cudaError_t launch_dd_back_scratch(const CtGrid &g, const CtView *views, int in_t, const void *in,
+                                   int out_t, void *out, int batch, float *scratch, cudaStream_t st);
+
 // Stream-ordered scratch from a library-owned pool on the current device
 // (memory is kept in the pool between calls, so steady-state calls do not
 // reach the driver's allocator).

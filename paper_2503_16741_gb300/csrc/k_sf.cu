@@ -732,6 +732,35 @@ cudaError_t dd_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
 }
 }  // namespace
 
+// DD backprojection in circular geometry into caller-provided scratch of at
+// least batch x nview x nv x nu floats (no allocation).
+cudaError_t launch_dd_back_scratch(const CtGrid &g, const CtView *views, int in_t, const void *in,
+                                   int out_t, void *out, int batch, float *scratch, cudaStream_t st) {
+    const size_t n = (size_t)g.nview * g.nv * g.nu * batch;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152u * 64u);
+    const bool curved = g.variant == GEO_CIRC_CURVED;
+    switch (in_t) {
+    case 0:
+        curved ? dd_prescale<float, true><<<blocks, 256, 0, st>>>(g, views, (const float *)in, scratch, batch)
+               : dd_prescale<float, false><<<blocks, 256, 0, st>>>(g, views, (const float *)in, scratch, batch);
+        break;
+    case 1:
+        curved ? dd_prescale<__half, true><<<blocks, 256, 0, st>>>(g, views, (const __half *)in, scratch, batch)
+               : dd_prescale<__half, false><<<blocks, 256, 0, st>>>(g, views, (const __half *)in, scratch, batch);
+        break;
+    default:
+        curved ? dd_prescale<__nv_bfloat16, true><<<blocks, 256, 0, st>>>(g, views, (const __nv_bfloat16 *)in,
+                                                                          scratch, batch)
+               : dd_prescale<__nv_bfloat16, false><<<blocks, 256, 0, st>>>(g, views, (const __nv_bfloat16 *)in,
+                                                                           scratch, batch);
+        break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return curved ? fp_back_circ<float, true, true>(g, views, scratch, out, out_t, batch, st)
+                  : fp_back_circ<float, false, true>(g, views, scratch, out, out_t, batch, st);
+}
+
 cudaError_t launch_sf(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st) {
     switch (in_t) {

@@ -94,6 +94,6 @@ def test_mbir_gradient_descent_reduces_the_data_term(ct):
         loss = torch.nn.functional.mse_loss(A(x), sino)
         (grad,) = torch.autograd.grad(loss, [x])
         x.data -= grad / L
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert all(b < a for a, b in zip(losses, losses[1:])), losses
     assert losses[-1] < 0.5 * losses[0], losses
