@@ -130,6 +130,81 @@ def cpu_oracle_sample(spec, nviews: int, x=None):
     return upd / dt / 1e9, dt, oracle.max_threads(), f"{nviews} of {spec.nview} views, full volume"
 
 
+def _gdict(spec):
+    return {k: getattr(spec, k) for k in ("kind", "det", "nx", "ny", "nz", "dx", "dy", "dz", "nu",
+                                          "nv", "du", "dv", "nview", "theta", "phi", "psi", "sad",
+                                          "sdd", "x_src", "z_src", "x_ofst", "y_ofst", "z_ofst",
+                                          "u_ofst", "v_ofst")}
+
+
+def serving_mix(n_req: int, seed: int = 0):
+    """Requests mixing the four geometry kinds, volumes of 64^3-256^3 (2D:
+    128^2-512^2), 90-360 views, and fwd (40 %) / back (40 %) / 10-step MBIR
+    (20 %) with the SF or DD projector; (request, voxel-view updates)."""
+    import numpy as np
+
+    import workloads as W
+    from paper_2503_16741_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    kinds = [("fan2d", W.fan2d_small(360)), ("circ", W.circ3d_256()), ("curved", W.circ3d_curved()),
+             ("noncirc", W.noncirc3d_saddle(360))]
+    out = []
+    for _ in range(n_req):
+        name, base = kinds[rng.integers(4)]
+        views = int(rng.choice([90, 180, 360]))
+        if name == "fan2d":
+            spec = W.scaled(base, int(rng.choice([128, 256, 512])), views)
+        else:
+            spec = W.scaled(base, int(rng.choice([64, 128, 256])), views)
+        op = rng.choice(["fwd", "back", "mbir"], p=[0.4, 0.4, 0.2])
+        proj = str(rng.choice(["sf", "dd"]))
+        vol = (spec.ny, spec.nx) if spec.kind == "fan2d" else spec.vol_shape
+        sino = (spec.nview, spec.nu) if spec.kind == "fan2d" else spec.sino_shape
+        data = rng.random(vol if op == "fwd" else sino, dtype=np.float32)
+        passes = 1 if op != "mbir" else 20
+        out.append((Request(_gdict(spec), str(op), data, projector=proj, iters=10),
+                    passes * spec.n_vox * spec.nview))
+    return out
+
+
+def serving_bench(dev_index: int, n_req: int, dtype: str = "f32"):
+    """Closed-loop saturation, then open-loop Poisson arrivals at 0.8 of it."""
+    import numpy as np
+
+    from paper_2503_16741_gb300.serve import Server, drive, poisson_arrivals
+    mix = serving_mix(n_req)
+    for r, _ in mix:
+        r.dtype = dtype
+    srv = Server(device=dev_index, slots=4, hbm_budget=48 << 30, max_batch=4)
+    for r, _ in mix:  # geometries and MBIR step sizes resident before timing
+        srv.ex.geometry(r.geometry)
+        if r.op == "mbir":
+            srv.ex.step_size(r.geometry, r.projector)
+    t0 = time.perf_counter()
+    futs = [srv.submit(r) for r, _ in mix]
+    for f in futs:
+        f.result(timeout=300)
+    t_sat = time.perf_counter() - t0
+    srv.close()
+    sat_rps = n_req / t_sat
+    upd = sum(u for _, u in mix)
+    srv = Server(device=dev_index, slots=4, hbm_budget=48 << 30, max_batch=4)
+    srv.ex._geoms = {}
+    arr = poisson_arrivals(0.8 * sat_rps, n_req, seed=1)
+    t0 = time.perf_counter()
+    futs = drive(srv, [r for r, _ in mix], arr)
+    for f in futs:
+        f.result(timeout=300)
+    t_open = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return {"dtype": dtype, "requests": n_req, "saturation_req_per_s": sat_rps,
+            "saturation_gupdates_per_s": upd / t_sat / 1e9,
+            "offered_req_per_s": 0.8 * sat_rps, "served_req_per_s": n_req / t_open,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "launches": st["launches"],
+            "hbm_peak_bytes": st["hbm_peak_bytes"]}
+
+
 def run_reference(args):
     """The oracle as the reference arm: K timed steps of a bounded sample."""
     ws, rank, _ = _dist()
@@ -165,6 +240,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-views", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=80)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -279,6 +356,13 @@ def main():
         "gpu_launches": 2 * K,
         "clocks": clk,
     }
+    if not args.no_serving:
+        torch.cuda.synchronize(dev)
+        out["serving"] = [serving_bench(local, args.serve_requests, "f32"),
+                          serving_bench(local, args.serve_requests, "f16")]
+        out["serving_mix"] = ("Poisson arrivals at 0.8 x measured saturation; fan-beam 128^2-512^2 and "
+                              "circular flat / circular curved / saddle non-circular 64^3-256^3 volumes, "
+                              "90-360 views, fwd 40% / back 40% / 10-step MBIR 20%, SF or DD")
     if ws == 1 and not args.no_cpu_baseline:
         val, dt, cores, sample = cpu_oracle_sample(spec, 8)
         out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -153,6 +153,24 @@ ct_status ct_back(const ct_geometry *geom, ct_projector proj, ct_mode mode,
                   ct_dtype in_t, const void *sino, ct_dtype out_t, void *vol,
                   int batch, void *cuda_stream);
 
+/* Accumulating forms, for iterative reconstruction (Sec. 2.4: the MBIR
+ * gradient step x <- x - lr A^T (A x - y) is one ct_forward_acc with
+ * alpha = 1, beta = -1 into a copy of y, then one ct_back_acc with
+ * alpha = -lr, beta = 1 into x):
+ *   ct_forward_acc:  sino = alpha * A vol   + beta * sino
+ *   ct_back_acc:     vol  = alpha * A^T sino + beta * vol
+ * Each output element is read (when beta != 0) and written once by the
+ * thread that computes it, so the update is in place; the old value is read
+ * in out_t and the sum rounded once to out_t.  alpha = 1, beta = 0 is
+ * ct_forward / ct_back exactly.  Other arguments, ownership and errors as for
+ * ct_forward / ct_back; alpha and beta must be finite. */
+ct_status ct_forward_acc(const ct_geometry *geom, ct_projector proj, ct_mode mode,
+                         ct_dtype in_t, const void *vol, ct_dtype out_t, void *sino,
+                         int batch, float alpha, float beta, void *cuda_stream);
+ct_status ct_back_acc(const ct_geometry *geom, ct_projector proj, ct_mode mode,
+                      ct_dtype in_t, const void *sino, ct_dtype out_t, void *vol,
+                      int batch, float alpha, float beta, void *cuda_stream);
+
 /* Distance-driven backprojection (as ct_back with CT_DD, CT_MODE_PROJ) that
  * allocates no device memory.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc or take memory from a pool

@@ -83,6 +83,11 @@ def load():
         sig = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
         lib.ct_forward.argtypes = sig
         lib.ct_back.argtypes = sig
+        sig_acc = sig[:-1] + [C.c_float, C.c_float, C.c_void_p]
+        lib.ct_forward_acc.argtypes = sig_acc
+        lib.ct_back_acc.argtypes = sig_acc
+        lib.ct_forward_acc.restype = C.c_int
+        lib.ct_back_acc.restype = C.c_int
         lib.ct_back_dd_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                            C.c_int, C.c_void_p]
         lib.ct_back_dd_noalloc.restype = C.c_int
@@ -221,6 +226,34 @@ def back_into(geom: Geometry, y: torch.Tensor, x: torch.Tensor, projector: str =
         raise ValueError("volume and sinogram batch sizes differ")
     _check(load().ct_back(geom.handle, PROJECTORS[projector], MODES[mode], DTYPES[y.dtype],
                           y.data_ptr(), DTYPES[x.dtype], x.data_ptr(), b, _stream_ptr(stream)))
+    return x
+
+
+def forward_acc(geom: Geometry, x: torch.Tensor, y: torch.Tensor, alpha: float, beta: float,
+                projector: str = "sf", mode: str = "proj", stream=None) -> torch.Tensor:
+    """y <- alpha A x + beta y, in place (y's dtype is the storage type)."""
+    _check_tensor(x, "volume")
+    _check_tensor(y, "sinogram")
+    b = _batch_of(x, geom.vol_shape, "volume")
+    if _batch_of(y, geom.sino_shape, "sinogram") != b:
+        raise ValueError("volume and sinogram batch sizes differ")
+    _check(load().ct_forward_acc(geom.handle, PROJECTORS[projector], MODES[mode], DTYPES[x.dtype],
+                                 x.data_ptr(), DTYPES[y.dtype], y.data_ptr(), b, float(alpha),
+                                 float(beta), _stream_ptr(stream)))
+    return y
+
+
+def back_acc(geom: Geometry, y: torch.Tensor, x: torch.Tensor, alpha: float, beta: float,
+             projector: str = "sf", mode: str = "proj", stream=None) -> torch.Tensor:
+    """x <- alpha A^T y + beta x, in place."""
+    _check_tensor(y, "sinogram")
+    _check_tensor(x, "volume")
+    b = _batch_of(y, geom.sino_shape, "sinogram")
+    if _batch_of(x, geom.vol_shape, "volume") != b:
+        raise ValueError("volume and sinogram batch sizes differ")
+    _check(load().ct_back_acc(geom.handle, PROJECTORS[projector], MODES[mode], DTYPES[y.dtype],
+                              y.data_ptr(), DTYPES[x.dtype], x.data_ptr(), b, float(alpha),
+                              float(beta), _stream_ptr(stream)))
     return x
 
 

@@ -243,6 +243,8 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
     G.is2d = two_d ? 1 : 0;
     G.variant = d->kind == CT_NONCIRC3D ? ctp::GEO_NONCIRC_FLAT
                                         : (curved ? ctp::GEO_CIRC_CURVED : ctp::GEO_CIRC_FLAT);
+    G.alpha = 1.f;
+    G.beta = 0.f;
     G.max_m_sf_u = 0.f;
     G.max_m_dd_u = 0.f;
     for (const CtView &V : g->host_views) {
@@ -309,7 +311,8 @@ static ct_status check_ptr(const void *p, const char *what) {
 }
 
 static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t,
-                         const void *in, ct_dtype out_t, void *out, int batch, void *stream) {
+                         const void *in, ct_dtype out_t, void *out, int batch, float alpha, float beta,
+                         void *stream) {
     if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");
     if (proj < CT_VOXEL || proj > CT_SF) return fail(CT_ERR_INVALID_ARG, "unknown projector");
     if (mode == CT_MODE_RECON) return fail(CT_ERR_UNSUPPORTED, "recon mode (FBP depth weighting) is not provided");
@@ -331,13 +334,17 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     if (st != CT_OK) return st;
     st = check_ptr(out, "output");
     if (st != CT_OK) return st;
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return fail(CT_ERR_INVALID_ARG, "alpha and beta must be finite");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CtGrid G = g->grid;
+    G.alpha = alpha;
+    G.beta = beta;
     cudaError_t e;
     switch (proj) {
-    case CT_VOXEL: e = ctp::launch_voxel(dir, g->grid, g->dev_views, in_t, in, out_t, out, batch, s); break;
-    case CT_RAY: e = ctp::launch_ray(dir, g->grid, g->dev_views, in_t, in, out_t, out, batch, s); break;
-    case CT_DD: e = ctp::launch_dd(dir, g->grid, g->dev_views, in_t, in, out_t, out, batch, s); break;
-    default: e = ctp::launch_sf(dir, g->grid, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    case CT_VOXEL: e = ctp::launch_voxel(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    case CT_RAY: e = ctp::launch_ray(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    case CT_DD: e = ctp::launch_dd(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    default: e = ctp::launch_sf(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     }
     if (e == cudaErrorMemoryAllocation) return fail(CT_ERR_OOM, "workspace allocation failed");
     if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
@@ -346,12 +353,22 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
 
 ct_status ct_forward(const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t, const void *vol,
                      ct_dtype out_t, void *sino, int batch, void *cuda_stream) {
-    return project(0, g, proj, mode, in_t, vol, out_t, sino, batch, cuda_stream);
+    return project(0, g, proj, mode, in_t, vol, out_t, sino, batch, 1.f, 0.f, cuda_stream);
 }
 
 ct_status ct_back(const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t, const void *sino,
                   ct_dtype out_t, void *vol, int batch, void *cuda_stream) {
-    return project(1, g, proj, mode, in_t, sino, out_t, vol, batch, cuda_stream);
+    return project(1, g, proj, mode, in_t, sino, out_t, vol, batch, 1.f, 0.f, cuda_stream);
+}
+
+ct_status ct_forward_acc(const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t, const void *vol,
+                         ct_dtype out_t, void *sino, int batch, float alpha, float beta, void *cuda_stream) {
+    return project(0, g, proj, mode, in_t, vol, out_t, sino, batch, alpha, beta, cuda_stream);
+}
+
+ct_status ct_back_acc(const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t, const void *sino,
+                      ct_dtype out_t, void *vol, int batch, float alpha, float beta, void *cuda_stream) {
+    return project(1, g, proj, mode, in_t, sino, out_t, vol, batch, alpha, beta, cuda_stream);
 }
 
 }  // extern "C"

@@ -33,6 +33,22 @@ __device__ __forceinline__ void st(void *out, size_t i, float v, int out_t) {
         static_cast<__nv_bfloat16 *>(out)[i] = __float2bfloat16_rn(v);
 }
 
+// plain (coherent) loads of the output buffer for the accumulate epilogue
+__device__ __forceinline__ float ldo_f(const void *p, size_t i, int t) {
+    if (t == 0) return static_cast<const float *>(p)[i];
+    if (t == 1) return __half2float(static_cast<const __half *>(p)[i]);
+    return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+}
+// Output epilogue: out = alpha * value + beta * out (beta = 0: out is only
+// written; alpha = 1, beta = 0 stores the value unchanged).  Each element is
+// read and written by the thread that produced it, so out may be updated in
+// place.
+__device__ __forceinline__ void st_out(const CtGrid &g, void *out, size_t i, float v, int out_t) {
+    float r = g.alpha * v;
+    if (g.beta != 0.f) r = fmaf(g.beta, ldo_f(out, i, out_t), r);
+    st(out, i, r, out_t);
+}
+
 // ---------------------------------------------------------------- intervals
 __device__ __forceinline__ float overlap(float lo1, float hi1, float lo2, float hi2) {
     return fmaxf(fminf(hi1, hi2) - fmaxf(lo1, lo2), 0.f);

@@ -95,7 +95,7 @@ dd_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
     }
 }
 
@@ -133,7 +133,7 @@ dd_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vo
             }
         }
     }
-    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc * dd_len<false>(V, g, a, b), out_t);
+    st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc * dd_len<false>(V, g, a, b), out_t);
 }
 
 // ------------------------------------------------------------ launchers

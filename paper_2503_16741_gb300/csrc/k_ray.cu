@@ -110,7 +110,7 @@ ray_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
         }
         acc *= len;
     }
-    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+    st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
 }
 
 // ------------------------------------------------------------ back (gather)
@@ -243,7 +243,7 @@ ray_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict_
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
     }
 }
 
@@ -316,7 +316,7 @@ ray_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
     }
 }
 

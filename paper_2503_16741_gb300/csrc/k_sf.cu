@@ -266,7 +266,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < kend) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk] + Gs[kk][tid], out_t);
+        if (k < kend) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk] + Gs[kk][tid], out_t);
     }
 }
 
@@ -324,7 +324,7 @@ sf_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
     }
 }
 
@@ -493,7 +493,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
         for (int r = 0; r < RPT; ++r) {
             const int b = B0 + threadIdx.y + 8 * r;
             if (b < g.nv)
-                st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
+                st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
                    DD ? acc[r] * dd_len<CURVED>(V, g, a, b) : acc[r], out_t);
         }
     }
@@ -578,7 +578,7 @@ sf_fwd_circ_wide(CtGrid g, const CtView *__restrict__ views, const TIn *__restri
         }
     }
     if (active)
-        st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
+        st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
            DD ? acc * dd_len<CURVED>(V, g, a, b) : acc, out_t);
 }
 
@@ -616,7 +616,7 @@ sf_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vo
             }
         }
     }
-    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+    st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
 }
 
 // ------------------------------------------------------------ DD cell factor

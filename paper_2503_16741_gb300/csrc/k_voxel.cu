@@ -126,7 +126,7 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
     }
 }
 
@@ -162,7 +162,7 @@ vx_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st(vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
     }
 }
 
@@ -215,7 +215,7 @@ vx_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
             }
         }
     }
-    st(sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
+    st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a, acc, out_t);
 }
 
 // ------------------------------------------------------------ launchers

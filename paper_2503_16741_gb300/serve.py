@@ -1,0 +1,375 @@
+"""Continuous-batching projection server.
+
+Requests -- a forward projection, a backprojection or a short MBIR solve
+(least-squares gradient descent, Sec. 2.4) on any geometry of Sec. 2.2 --
+arrive at any time from any thread.  A scheduler thread admits them while a
+slot (a CUDA stream) is free and the device memory they need fits the HBM
+budget, so requests that arrive while others run start as soon as resources
+free up and their work overlaps on the device.  Waiting requests with the
+same geometry, operation, projector and storage type are merged into one
+batched launch (the kernels treat batch items independently and
+deterministically, so each result is the same alone and in a batch).
+Geometry tables stay resident on the device between requests.
+
+The scheduler is independent of the device: `Scheduler` drives an
+`Executor` (launch a group, poll it, collect results).  `GpuExecutor` runs
+the library's kernels; tests drive the scheduler with a host-only executor.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import dataclasses
+import threading
+import time
+from typing import Any, Callable, Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+OPS = ("fwd", "back", "mbir")
+ITEMSIZE = {"f32": 4, "f16": 2, "bf16": 2}
+
+
+@dataclasses.dataclass(eq=False)
+class Request:
+    """One job.  `geometry`: keyword arguments of `Geometry` (hashable once
+    frozen by `geometry_key`).  `data`: host array, the volume (fwd) or the
+    sinogram (back, mbir), shape (nz, ny, nx) / (nview, nv, nu) (2D: without
+    the z / v axis).  `dtype`: storage type on the device."""
+    geometry: Dict[str, Any]
+    op: str
+    data: np.ndarray
+    projector: str = "sf"
+    dtype: str = "f32"
+    iters: int = 10
+    deadline_s: Optional[float] = None
+
+
+def geometry_key(geom: Dict[str, Any]) -> Tuple:
+    items = []
+    for k in sorted(geom):
+        v = geom[k]
+        if isinstance(v, np.ndarray) or isinstance(v, (list, tuple)):
+            v = tuple(np.asarray(v, dtype=np.float64).ravel().tolist())
+        items.append((k, v))
+    return tuple(items)
+
+
+def shapes(geom: Dict[str, Any]):
+    two_d = geom["kind"] == "fan2d"
+    vol = (geom["ny"], geom["nx"]) if two_d else (geom["nz"], geom["ny"], geom["nx"])
+    sino = (geom["nview"], geom["nu"]) if two_d else (geom["nview"], geom["nv"], geom["nu"])
+    return vol, sino
+
+
+def request_bytes(req: Request) -> int:
+    """Device bytes a request holds while it runs: input, output and, for
+    MBIR, the residual sinogram."""
+    vol, sino = shapes(req.geometry)
+    nv, ns = int(np.prod(vol)), int(np.prod(sino))
+    it = ITEMSIZE[req.dtype]
+    if req.op == "fwd":
+        return (nv + ns) * it
+    if req.op == "back":
+        return (ns + nv) * it
+    return (2 * ns + nv) * it
+
+
+def group_key(req: Request) -> Tuple:
+    return (geometry_key(req.geometry), req.op, req.projector, req.dtype,
+            req.iters if req.op == "mbir" else 0)
+
+
+@dataclasses.dataclass(eq=False)
+class _Pending:
+    req: Request
+    fut: cf.Future
+    t_submit: float
+    nbytes: int
+
+
+class Executor:
+    """Runs groups of compatible requests.  launch() returns a handle;
+    done(handle) polls it; results(handle) returns one host array per
+    request; release(handle) frees its device memory."""
+
+    slots = 1
+
+    def launch(self, slot: int, reqs: Sequence[Request]):  # pragma: no cover - interface
+        raise NotImplementedError
+
+    def done(self, handle) -> bool:  # pragma: no cover - interface
+        raise NotImplementedError
+
+    def results(self, handle) -> List[np.ndarray]:  # pragma: no cover - interface
+        raise NotImplementedError
+
+    def release(self, handle) -> None:
+        pass
+
+
+class Scheduler:
+    """Admission (slots, HBM budget, FIFO with grouping), completion
+    polling, deadlines and cancellation."""
+
+    def __init__(self, executor: Executor, hbm_budget: int, max_batch: int = 8,
+                 group_window: int = 64, poll_s: float = 2e-4):
+        self.ex = executor
+        self.budget = int(hbm_budget)
+        self.max_batch = max_batch
+        self.group_window = group_window
+        self.poll_s = poll_s
+        self._lock = threading.Condition()
+        self._queue: collections.deque = collections.deque()
+        self._free_slots = list(range(executor.slots))
+        self._inflight: List[Tuple[Any, int, List[_Pending], int]] = []
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.latencies: List[float] = []
+        self.completed = 0
+        self.rejected = 0
+        self.timed_out = 0
+        self.launches = 0
+        self._stop = False
+        self._thread = threading.Thread(target=self._run, name="ct-scheduler", daemon=True)
+        self._thread.start()
+
+    # ---- client side
+    def submit(self, req: Request) -> cf.Future:
+        fut: cf.Future = cf.Future()
+        if req.op not in OPS:
+            fut.set_exception(ValueError(f"unknown op {req.op!r}"))
+            return fut
+        nbytes = request_bytes(req)
+        with self._lock:
+            if nbytes > self.budget:
+                self.rejected += 1
+                fut.set_exception(MemoryError(
+                    f"request needs {nbytes} bytes, above the HBM budget of {self.budget}"))
+                return fut
+            self._queue.append(_Pending(req, fut, time.perf_counter(), nbytes))
+            self._lock.notify()
+        return fut
+
+    def queue_depth(self) -> int:
+        with self._lock:
+            return len(self._queue)
+
+    def close(self, wait: bool = True):
+        with self._lock:
+            self._stop = True
+            self._lock.notify()
+        if wait:
+            self._thread.join()
+
+    def stats(self) -> Dict[str, Any]:
+        with self._lock:
+            lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+            return {"completed": self.completed, "rejected": self.rejected,
+                    "timed_out": self.timed_out, "launches": self.launches,
+                    "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                    "hbm_peak_bytes": self.peak_in_use, "queue_depth": len(self._queue)}
+
+    # ---- scheduler thread
+    def _take_group(self) -> Optional[List[_Pending]]:
+        """Head of the queue plus compatible requests among the next
+        group_window waiting ones, within max_batch and the free budget."""
+        while self._queue and self._queue[0].fut.cancelled():
+            self._queue.popleft()
+        if not self._queue:
+            return None
+        head = self._queue[0]
+        if self.in_use + head.nbytes > self.budget:
+            return None
+        key = group_key(head.req)
+        group, total = [head], head.nbytes
+        for p in list(self._queue)[1:self.group_window]:
+            if len(group) >= self.max_batch:
+                break
+            if p.fut.cancelled() or group_key(p.req) != key:
+                continue
+            if self.in_use + total + p.nbytes > self.budget:
+                break
+            group.append(p)
+            total += p.nbytes
+        for p in group:
+            self._queue.remove(p)
+        return group
+
+    def _complete(self, handle, slot, group, nbytes):
+        try:
+            outs = self.ex.results(handle)
+            err = None
+        except Exception as e:  # noqa: BLE001 - reported on every future of the group
+            outs, err = None, e
+        self.ex.release(handle)
+        now = time.perf_counter()
+        with self._lock:
+            self.in_use -= nbytes
+            self._free_slots.append(slot)
+            for k, p in enumerate(group):
+                if p.fut.done():
+                    continue
+                if err is not None:
+                    p.fut.set_exception(err)
+                else:
+                    p.fut.set_result(outs[k])
+                    self.latencies.append(now - p.t_submit)
+                    self.completed += 1
+
+    def _run(self):
+        while True:
+            progressed = False
+            # completions and deadlines
+            for item in list(self._inflight):
+                handle, slot, group, nbytes = item
+                if self.ex.done(handle):
+                    self._inflight.remove(item)
+                    self._complete(handle, slot, group, nbytes)
+                    progressed = True
+                else:
+                    now = time.perf_counter()
+                    for p in group:
+                        if (p.req.deadline_s is not None and not p.fut.done()
+                                and now - p.t_submit > p.req.deadline_s):
+                            p.fut.set_exception(TimeoutError("deadline passed before completion"))
+                            with self._lock:
+                                self.timed_out += 1
+            # admissions (the launch itself runs outside the lock so that
+            # clients can keep submitting)
+            while True:
+                with self._lock:
+                    if not self._free_slots:
+                        break
+                    group = self._take_group()
+                    if group is None:
+                        break
+                    slot = self._free_slots.pop()
+                    nbytes = sum(p.nbytes for p in group)
+                    self.in_use += nbytes
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                try:
+                    handle = self.ex.launch(slot, [p.req for p in group])
+                except Exception as e:  # noqa: BLE001 - a failed launch rejects its group
+                    with self._lock:
+                        self.in_use -= nbytes
+                        self._free_slots.append(slot)
+                        self.rejected += len(group)
+                    for p in group:
+                        if not p.fut.done():
+                            p.fut.set_exception(e)
+                    continue
+                with self._lock:
+                    self.launches += 1
+                self._inflight.append((handle, slot, group, nbytes))
+                progressed = True
+            with self._lock:
+                if self._stop and not self._queue and not self._inflight:
+                    return
+                if not progressed:
+                    self._lock.wait(timeout=self.poll_s)
+
+
+class GpuExecutor(Executor):
+    """Runs groups on one GPU with the library's kernels: one CUDA stream
+    per slot; pinned host staging; geometries cached on the device; MBIR
+    steps fused into ct_forward_acc / ct_back_acc."""
+
+    def __init__(self, device: int = 0, slots: int = 4):
+        import torch
+
+        from .binding import Geometry
+        self.torch = torch
+        self.Geometry = Geometry
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.slots = slots
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self._geoms: Dict[Tuple, Any] = {}
+        self._lr: Dict[Tuple, float] = {}
+        self._dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+
+    def geometry(self, g: Dict[str, Any]):
+        key = geometry_key(g)
+        if key not in self._geoms:
+            self.torch.cuda.set_device(self.device)
+            self._geoms[key] = self.Geometry(**g)
+        return self._geoms[key]
+
+    def step_size(self, g: Dict[str, Any], projector: str) -> float:
+        from .mbir import ls_step_size
+        key = (geometry_key(g), projector)
+        if key not in self._lr:
+            self._lr[key] = ls_step_size(self.geometry(g), projector)
+        return self._lr[key]
+
+    def launch(self, slot: int, reqs: Sequence[Request]):
+        from .binding import back_into, forward_into
+        from .mbir import ls_gradient_descent
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        r0 = reqs[0]
+        geom = self.geometry(r0.geometry)
+        lr = self.step_size(r0.geometry, r0.projector) if r0.op == "mbir" else None
+        vol, sino = shapes(r0.geometry)
+        in_shape = vol if r0.op == "fwd" else sino
+        for r in reqs:
+            if tuple(r.data.shape) != tuple(in_shape):
+                raise ValueError(f"input shape {r.data.shape} != {in_shape}")
+        dt = self._dt[r0.dtype]
+        stream = self.streams[slot]
+        host_in = torch.from_numpy(np.stack([np.asarray(r.data, dtype=np.float32) for r in reqs]))
+        host_in = host_in.to(dt).pin_memory()
+        with torch.cuda.stream(stream):
+            d_in = host_in.to(self.device, non_blocking=True)
+            if r0.op == "fwd":
+                d_out = torch.empty((len(reqs),) + sino, dtype=dt, device=self.device)
+                forward_into(geom, d_in, d_out, r0.projector, stream=stream)
+            elif r0.op == "back":
+                d_out = torch.empty((len(reqs),) + vol, dtype=dt, device=self.device)
+                back_into(geom, d_in, d_out, r0.projector, stream=stream)
+            else:
+                d_out = ls_gradient_descent(geom, d_in, r0.projector, r0.iters, lr=lr, stream=stream)
+            host_out = torch.empty(d_out.shape, dtype=dt).pin_memory()
+            host_out.copy_(d_out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        # keep device buffers alive until the event has passed
+        return {"event": ev, "host_out": host_out, "keep": (d_in, d_out, host_in)}
+
+    def done(self, handle) -> bool:
+        return handle["event"].query()
+
+    def results(self, handle) -> List[np.ndarray]:
+        out = handle["host_out"].float().numpy()
+        return [out[k].copy() for k in range(out.shape[0])]
+
+    def release(self, handle) -> None:
+        handle["keep"] = None
+
+
+class Server(Scheduler):
+    """A Scheduler over a GpuExecutor."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 32 << 30,
+                 max_batch: int = 8, **kw):
+        super().__init__(GpuExecutor(device, slots), hbm_budget, max_batch=max_batch, **kw)
+
+
+def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson process."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, n))
+
+
+def drive(sched: Scheduler, reqs: Sequence[Request], arrivals: Sequence[float],
+          clock: Callable[[], float] = time.perf_counter) -> List[cf.Future]:
+    """Submit each request at its arrival time (relative to now)."""
+    t0 = clock()
+    futs = []
+    for r, t in zip(reqs, arrivals):
+        while clock() - t0 < t:
+            time.sleep(min(1e-3, max(0.0, t - (clock() - t0))))
+        futs.append(sched.submit(r))
+    return futs
