@@ -289,6 +289,21 @@ class GpuExecutor(Executor):
         self._geoms: Dict[Tuple, Any] = {}
         self._lr: Dict[Tuple, float] = {}
         self._dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+        self._pinned: Dict[Tuple, List[Any]] = collections.defaultdict(list)
+        self._plock = threading.Lock()
+
+    def _pinned_buffer(self, shape, dtype):
+        """A pinned host buffer from a pool keyed by shape and dtype
+        (page-locking memory per request would cost more than the copy)."""
+        key = (tuple(shape), dtype)
+        with self._plock:
+            if self._pinned[key]:
+                return self._pinned[key].pop()
+        return self.torch.empty(shape, dtype=dtype).pin_memory()
+
+    def _return_pinned(self, buf):
+        with self._plock:
+            self._pinned[(tuple(buf.shape), buf.dtype)].append(buf)
 
     def geometry(self, g: Dict[str, Any]):
         key = geometry_key(g)
@@ -319,8 +334,9 @@ class GpuExecutor(Executor):
                 raise ValueError(f"input shape {r.data.shape} != {in_shape}")
         dt = self._dt[r0.dtype]
         stream = self.streams[slot]
-        host_in = torch.from_numpy(np.stack([np.asarray(r.data, dtype=np.float32) for r in reqs]))
-        host_in = host_in.to(dt).pin_memory()
+        host_in = self._pinned_buffer((len(reqs),) + tuple(in_shape), dt)
+        for k, r in enumerate(reqs):
+            host_in[k].copy_(torch.from_numpy(np.asarray(r.data, dtype=np.float32)))
         with torch.cuda.stream(stream):
             d_in = host_in.to(self.device, non_blocking=True)
             if r0.op == "fwd":
@@ -331,12 +347,12 @@ class GpuExecutor(Executor):
                 back_into(geom, d_in, d_out, r0.projector, stream=stream)
             else:
                 d_out = ls_gradient_descent(geom, d_in, r0.projector, r0.iters, lr=lr, stream=stream)
-            host_out = torch.empty(d_out.shape, dtype=dt).pin_memory()
+            host_out = self._pinned_buffer(tuple(d_out.shape), dt)
             host_out.copy_(d_out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
         # keep device buffers alive until the event has passed
-        return {"event": ev, "host_out": host_out, "keep": (d_in, d_out, host_in)}
+        return {"event": ev, "host_out": host_out, "host_in": host_in, "keep": (d_in, d_out)}
 
     def done(self, handle) -> bool:
         return handle["event"].query()
@@ -347,14 +363,19 @@ class GpuExecutor(Executor):
 
     def release(self, handle) -> None:
         handle["keep"] = None
+        for k in ("host_in", "host_out"):
+            if handle.get(k) is not None:
+                self._return_pinned(handle[k])
+                handle[k] = None
 
 
 class Server(Scheduler):
-    """A Scheduler over a GpuExecutor."""
+    """A Scheduler over a GpuExecutor (pass `executor` to keep its resident
+    geometries, step sizes and pinned buffers across servers)."""
 
     def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 32 << 30,
-                 max_batch: int = 8, **kw):
-        super().__init__(GpuExecutor(device, slots), hbm_budget, max_batch=max_batch, **kw)
+                 max_batch: int = 8, executor: Optional[GpuExecutor] = None, **kw):
+        super().__init__(executor or GpuExecutor(device, slots), hbm_budget, max_batch=max_batch, **kw)
 
 
 def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:
