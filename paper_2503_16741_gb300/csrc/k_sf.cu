@@ -145,7 +145,7 @@ template <typename TIn, bool CURVED, bool DD, int ZT>
 __global__ void __launch_bounds__(128, 7)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
-    constexpr int NR = ZT + 4;  // rows one chunk can touch (|sv| < 1), with a guard row each side
+    constexpr int NR = ZT + 3;  // rows -1 .. ZT + 1 relative to the chunk's first voxel
     __shared__ CtView sview[kViews];
     __shared__ float Rs[NR][128];
     __shared__ float Gs[ZT][128];  // general-path partial sums (thread-private slots)
@@ -181,7 +181,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             d1 = min(d1, g.nu - 1 - C.aref);
             if (d0 > d1) continue;
             const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
-            if (d1 - d0 <= 3 && C.hv < 0.5f && g.nu >= 4) {
+            if (d1 - d0 <= 3 && C.hv < 0.5f && C.sv > 0.f && g.nu >= 4) {
                 float F[4];
                 trap_cells4(C.T, d0, d1, F);
                 // 4-cell window [as, as + 3] inside the detector; shift the
@@ -197,35 +197,37 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                     for (int p = 0; p < 4; ++p) w = (q - sh == p) ? F[p] : w;
                     Fu[q] = w;
                 }
-                // rows touched by the chunk, one guard row each side
-                const float fa = fmaf(C.sv, (float)kbeg, C.fv0), fb = fmaf(C.sv, (float)(kend - 1), C.fv0);
-                const int rb0 = (int)floorf(fminf(fa, fb) - C.hv + 0.5f) - 1;
-                const int nr = min(NR, (int)floorf(fmaxf(fa, fb) + C.hv + 0.5f) + 2 - rb0);
+                // Rows relative to the chunk's first voxel: voxel kk sits at
+                // rel = frac0 + sv kk rows from row bref0 (0 < sv < 1), so it
+                // touches rows e0, e0 + 1 with e0 in [-1, ZT - 1].
+                int bref0;
+                float frac0;
+                split_cell(fmaf(C.sv, (float)kbeg, C.fv0), bref0, frac0);
+                const float last = fmaf(C.sv, (float)(kend - 1 - kbeg), frac0);
+                const int ef = (int)floorf(frac0 - C.hv + 0.5f), el = (int)floorf(last + C.hv + 0.5f);
+                const int va = max(ef, -bref0), vb = min(el, g.nv - 1 - bref0);  // rows on the detector
                 const TIn *ya = yv + as;
+                for (int e = ef; e < va; ++e) Rs[e + 1][tid] = 0.f;
 #pragma unroll 4
-                for (int r = 0; r < nr; ++r) {
-                    const int b = rb0 + r;
-                    float R = 0.f;
-                    if (b >= 0 && b < g.nv) {
-                        const TIn *row = ya + (size_t)b * g.nu;
-                        R = Fu[0] * ld(row, 0);
-                        R = fmaf(Fu[1], ld(row, 1), R);
-                        R = fmaf(Fu[2], ld(row, 2), R);
-                        R = fmaf(Fu[3], ld(row, 3), R);
-                    }
-                    Rs[r][tid] = R;
+                for (int e = va; e <= vb; ++e) {
+                    const TIn *row = ya + (size_t)(bref0 + e) * g.nu;
+                    float R = Fu[0] * ld(row, 0);
+                    R = fmaf(Fu[1], ld(row, 1), R);
+                    R = fmaf(Fu[2], ld(row, 2), R);
+                    R = fmaf(Fu[3], ld(row, 3), R);
+                    Rs[e + 1][tid] = R;
                 }
+                for (int e = max(vb + 1, ef); e <= el + 1; ++e) Rs[e + 1][tid] = 0.f;
                 float fk = (float)kbeg;
 #pragma unroll
                 for (int kk = 0; kk < ZT; ++kk, fk += 1.f) {
                     if (kbeg + kk < kend) {
-                        int bref, e0;
-                        float vf, Fv0, Fv1;
-                        split_cell(fmaf(C.sv, fk, C.fv0), bref, vf);
-                        two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
-                        const int r0 = min(max(bref + e0 - rb0, 0), nr - 2);
+                        const float rel = fmaf(C.sv, (float)kk, frac0);
+                        int e0;
+                        float Fv0, Fv1;
+                        two_rows(rel - C.hv, rel + C.hv, e0, Fv0, Fv1);
                         const float wz = fmaf(fk, g.dz, V.o[2]);
-                        acc[kk] = fmaf(fp_amp<DD>(C, wz), fmaf(Fv0, Rs[r0][tid], Fv1 * Rs[r0 + 1][tid]),
+                        acc[kk] = fmaf(fp_amp<DD>(C, wz), fmaf(Fv0, Rs[e0 + 1][tid], Fv1 * Rs[e0 + 2][tid]),
                                        acc[kk]);
                     }
                 }
