@@ -23,6 +23,24 @@ template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat
     return __bfloat162float(__ldg(p + i));
 }
 
+// four consecutive elements from an address aligned to 4 elements
+__device__ __forceinline__ void ld4(const float *__restrict__ p, float v[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const __half *__restrict__ p, float v[4]) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16 *__restrict__ p, float v[4]) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // out_t: 0 = f32, 1 = f16, 2 = bf16; one rounding at the store
 __device__ __forceinline__ void st(void *out, size_t i, float v, int out_t) {
     if (out_t == 0)

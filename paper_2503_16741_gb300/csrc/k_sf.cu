@@ -354,7 +354,7 @@ template <int RPT> struct SfFwdSmem {
 template <typename TIn, bool CURVED, bool DD, int RPT>
 __global__ void __launch_bounds__(256, 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
-            void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
+            const TIn *__restrict__ volZ, void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
     constexpr int BV = 8 * RPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SfFwdSmem<RPT> &S = *reinterpret_cast<SfFwdSmem<RPT> *>(smem_raw);
@@ -427,7 +427,32 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 const int k1 = min(g.nz - 1, (int)floorf(fmaxf(ka, kb)));
                 const TIn *xc = x + (size_t)j * g.nx + i;
                 const size_t zs = (size_t)g.nx * g.ny;
-                if (C.hv < 0.5f) {
+                if (C.hv < 0.5f && volZ != nullptr) {
+                    // axial rectangle shorter than a row (at most two rows per
+                    // voxel); the column is contiguous in the z-major copy and
+                    // is read 4 voxels per load (nz is a multiple of 4)
+                    const TIn *cz = volZ + (size_t)bt * g.nx * g.ny * g.nz + ((size_t)j * g.nx + i) * g.nz;
+                    for (int kb = k0 & ~3; kb <= k1; kb += 4) {
+                        float xv[4];
+                        ld4(cz + kb, xv);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int k = kb + t;
+                            if (k < k0 || k > k1) continue;
+                            int bref;
+                            float vf;
+                            split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                            const float wz = fmaf((float)k, g.dz, V.o[2]);
+                            const float val = fp_amp<DD>(C, wz) * xv[t];
+                            int e0;
+                            float Fv0, Fv1;
+                            two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
+                            const int r0 = bref + e0 - B0;
+                            if (r0 >= 0 && r0 < BV) S.Z[r0][tid] = fmaf(Fv0, val, S.Z[r0][tid]);
+                            if (r0 + 1 >= 0 && r0 + 1 < BV) S.Z[r0 + 1][tid] = fmaf(Fv1, val, S.Z[r0 + 1][tid]);
+                        }
+                    }
+                } else if (C.hv < 0.5f) {
                     // axial rectangle shorter than a row: at most two rows per voxel
 #pragma unroll 4
                     for (int k = k0; k <= k1; ++k) {
@@ -472,8 +497,8 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                     if (S.cnt[t] == 0) continue;
                     const float fs = (float)(seg + t);
                     const float Bu = fmaf(sc.us, fs, sc.u3), Bn = fmaf(sc.ns, fs, sc.n3);
-                    const float la = (T1 * Bn - Bu) / (sc.ul - T1 * sc.nl);
-                    const float lb = (T2 * Bn - Bu) / (sc.ul - T2 * sc.nl);
+                    const float la = __fdividef(T1 * Bn - Bu, sc.ul - T1 * sc.nl);
+                    const float lb = __fdividef(T2 * Bn - Bu, sc.ul - T2 * sc.nl);
                     const int c0 = max((int)ceilf(fminf(la, lb)) - S.L0[t], 0);
                     const int c1 = min((int)floorf(fmaxf(la, lb)) - S.L0[t], S.cnt[t] - 1);
                     for (int c = c0; c <= c1; ++c) {
@@ -639,6 +664,30 @@ dd_prescale(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
     }
 }
 
+// ------------------------------------------------------------ z-major copy
+// xZ[b][j][i][k] = x[b][k][j][i]: each voxel column contiguous, for the
+// forward's column walks.  32 x 33 shared-memory tiles over (i, k).
+template <typename T>
+__global__ void __launch_bounds__(256)
+to_zmajor(const T *__restrict__ x, T *__restrict__ xZ, int nx, int ny, int nz) {
+    __shared__ T tile[32][33];
+    const int tiles_i = (nx + 31) / 32;
+    const int i0 = (blockIdx.x % tiles_i) * 32, k0 = (blockIdx.x / tiles_i) * 32;
+    const int j = blockIdx.y;
+    const size_t nvox = (size_t)nx * ny * nz;
+    const T *src = x + blockIdx.z * nvox;
+    T *dst = xZ + blockIdx.z * nvox;
+    for (int r = threadIdx.y; r < 32; r += 8) {  // rows of k, coalesced along i
+        const int k = k0 + r, i = i0 + threadIdx.x;
+        if (i < nx && k < nz) tile[r][threadIdx.x] = src[((size_t)k * ny + j) * nx + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {  // rows of i, coalesced along k
+        const int i = i0 + r, k = k0 + threadIdx.x;
+        if (i < nx && k < nz) dst[((size_t)j * nx + i) * nz + k] = tile[threadIdx.x][r];
+    }
+}
+
 // ------------------------------------------------------------ launchers
 namespace {
 constexpr int kZT = 16;
@@ -651,9 +700,28 @@ cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, 
     cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // a z-major copy of the volume (pooled workspace) makes every column walk
+    // a contiguous, vector-loaded read; without it the walks read strided
+    TIn *xZ = nullptr;
+    if (g.nz % 4 == 0 && g.nz >= 8) {
+        const size_t n = (size_t)g.nx * g.ny * g.nz * batch;
+        if (workspace_alloc((void **)&xZ, n * sizeof(TIn), st) != cudaSuccess) {
+            cudaGetLastError();
+            xZ = nullptr;
+        } else {
+            dim3 tb(32, 8), tg((unsigned)(((g.nx + 31) / 32) * ((g.nz + 31) / 32)), (unsigned)g.ny,
+                               (unsigned)batch);
+            to_zmajor<TIn><<<tg, tb, 0, st>>>(src, xZ, g.nx, g.ny, g.nz);
+        }
+    }
     dim3 blk(32, 8), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
-    sf_fwd_circ<TIn, CURVED, DD, RPT><<<grd, blk, smem, st>>>(g, views, src, out, out_t, tiles_u, tiles_v);
-    return cudaGetLastError();
+    sf_fwd_circ<TIn, CURVED, DD, RPT><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u, tiles_v);
+    e = cudaGetLastError();
+    if (xZ) {
+        const cudaError_t ef = workspace_free(xZ, st);
+        if (e == cudaSuccess) e = ef;
+    }
+    return e;
 }
 
 // forward, circular geometry
