@@ -211,6 +211,53 @@ def serving_bench(dev_index: int, n_req: int, dtype: str = "f32"):
             "hbm_peak_bytes": st["hbm_peak_bytes"]}
 
 
+def run_suite(args):
+    """Forward and back time of every projector on each workload (one JSON
+    line per case): GUpdates/s per direction at the storage types given."""
+    import torch
+
+    import paper_2503_16741_gb300 as ct
+    import workloads as W
+    from paper_2503_16741_gb300 import build as cbuild
+    cbuild.build()
+    torch.cuda.set_device(0)
+    dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    cases = [("fan2d 128^2, 180 views, 256 bins", W.fan2d_small(), ["ray", "voxel", "dd", "sf"], ["f32"]),
+             ("circ 256^3, 360 views, 512x384", W.circ3d_256(), ["sf", "dd", "voxel", "ray"], ["f32", "f16"]),
+             ("circ curved 512^2x128, 984 views, 888x64", W.circ3d_curved(), ["dd", "sf"], ["f32"]),
+             ("saddle 512^3, 500 views, 1024^2", W.noncirc3d_saddle(), ["sf", "dd"], ["f32", "f16", "bf16"])]
+    for name, spec, projs, dtypes in cases:
+        if args.suite_filter and args.suite_filter not in name:
+            continue
+        g = ct.Geometry.from_spec(spec)
+        for tname in dtypes:
+            x = W.phantom(spec, seed=0, device="cuda", dtype=dt[tname])
+            x = x.reshape(g.vol_shape)
+            y = torch.empty(g.sino_shape, dtype=dt[tname], device="cuda")
+            xb = torch.empty(g.vol_shape, dtype=dt[tname], device="cuda")
+            for proj in projs:
+                ct.forward_into(g, x, y, proj)
+                ct.back_into(g, y, xb, proj)
+                torch.cuda.synchronize()
+                reps = args.suite_reps
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                for _ in range(reps):
+                    ct.forward_into(g, x, y, proj)
+                e[1].record()
+                for _ in range(reps):
+                    ct.back_into(g, y, xb, proj)
+                e[2].record()
+                torch.cuda.synchronize()
+                tf, tb = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+                upd = spec.n_vox * spec.nview
+                print(json.dumps({"suite": name, "projector": proj, "dtype": tname,
+                                  "fwd_ms": tf, "back_ms": tb, "fwd_gups": upd / tf / 1e6,
+                                  "back_gups": upd / tb / 1e6,
+                                  "pair_gups": 2 * upd / (tf + tb) / 1e6}), flush=True)
+        g.close()
+
+
 def run_reference(args):
     """The oracle as the reference arm: K timed steps of a bounded sample."""
     ws, rank, _ = _dist()
@@ -248,9 +295,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=80)
+    ap.add_argument("--suite", action="store_true", help="time every projector on each workload")
+    ap.add_argument("--suite-reps", type=int, default=2)
+    ap.add_argument("--suite-filter", default="", help="only workloads whose name contains this")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite:
+        return run_suite(args)
 
     import torch
     import torch.distributed as dist

@@ -112,6 +112,18 @@ __device__ __forceinline__ void trap_cells4(const Trap &t, int d0, int d1, float
     for (int q = 0; q < 4; ++q) F[q] = (d0 + q <= d1) ? G[q + 1] - G[q] : 0.f;
 }
 
+// weights of the N cells d0 .. d0+N-1 (zero past d1); each equals trap_cell
+template <int N>
+__device__ __forceinline__ void trap_cellsN(const Trap &t, int d0, int d1, float F[N]) {
+    float Gp = trap_G(t, (float)d0 - 0.5f);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const float Gn = trap_G(t, (float)(d0 + q) + 0.5f);
+        F[q] = (d0 + q <= d1) ? Gn - Gp : 0.f;
+        Gp = Gn;
+    }
+}
+
 // Axial rectangle [lo, hi] of width < 1 row (relative to a row grid whose
 // row e covers [e - 1/2, e + 1/2]): it meets rows e0 and e0 + 1 only, with
 // the overlaps below (equal to overlap(lo, hi, e -+ 1/2) bit for bit).

@@ -344,20 +344,20 @@ sf_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 constexpr int kItems = 256;
 constexpr int kSlabSeg = 1024;
 
-template <int RPT> struct SfFwdSmem {
+template <int RPT, int NA> struct SfFwdSmem {
     float Z[8 * RPT][kItems];  // [row][item]: conflict-free in both stages
-    float Fu[4][kItems];
+    float Fu[NA][kItems];      // the item's NA transaxial cell weights
     int a0[kItems];
     int L0[kSlabSeg], cnt[kSlabSeg], off[kSlabSeg + 1];
 };
 
-template <typename TIn, bool CURVED, bool DD, int RPT>
+template <typename TIn, bool CURVED, bool DD, int RPT, int NA>
 __global__ void __launch_bounds__(256, 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
             const TIn *__restrict__ volZ, void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
     constexpr int BV = 8 * RPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SfFwdSmem<RPT> &S = *reinterpret_cast<SfFwdSmem<RPT> *>(smem_raw);
+    SfFwdSmem<RPT, NA> &S = *reinterpret_cast<SfFwdSmem<RPT, NA> *>(smem_raw);
     int bx = blockIdx.x;
     const int tu = bx % tiles_u; bx /= tiles_u;
     const int tv = bx % tiles_v; bx /= tiles_v;
@@ -411,10 +411,10 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 const int i = main_y ? l : s, j = main_y ? s : l;
                 const SfCol C = sf_col<CURVED, DD>(V, g, i, j);
                 int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
-                float Fu[4];
-                trap_cells4(C.T, d0, d1, Fu);
+                float Fu[NA];
+                trap_cellsN<NA>(C.T, d0, d1, Fu);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) S.Fu[r][tid] = Fu[r];
+                for (int r = 0; r < NA; ++r) S.Fu[r][tid] = Fu[r];
                 S.a0[tid] = C.aref + d0;
 #pragma unroll
                 for (int r = 0; r < BV; ++r) S.Z[r][tid] = 0.f;
@@ -505,7 +505,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         const int item = S.off[t] + c - base;
                         if (item < 0 || item >= kItems) continue;
                         const int d = a - S.a0[item];
-                        if (d < 0 || d > 3) continue;
+                        if (d < 0 || d >= NA) continue;
                         const float w = S.Fu[d][item];
 #pragma unroll
                         for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[threadIdx.y + 8 * r][item], acc[r]);
@@ -692,12 +692,12 @@ to_zmajor(const T *__restrict__ x, T *__restrict__ xZ, int nx, int ny, int nz) {
 namespace {
 constexpr int kZT = 16;
 
-template <typename TIn, bool CURVED, bool DD, int RPT>
+template <typename TIn, bool CURVED, bool DD, int RPT, int NA>
 cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                           int batch, cudaStream_t st) {
     const int tiles_u = (g.nu + 31) / 32, tiles_v = (g.nv + 8 * RPT - 1) / (8 * RPT);
-    const size_t smem = sizeof(SfFwdSmem<RPT>);
-    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT>,
+    const size_t smem = sizeof(SfFwdSmem<RPT, NA>);
+    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT, NA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a z-major copy of the volume (pooled workspace) makes every column walk
@@ -715,7 +715,8 @@ cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, 
         }
     }
     dim3 blk(32, 8), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
-    sf_fwd_circ<TIn, CURVED, DD, RPT><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u, tiles_v);
+    sf_fwd_circ<TIn, CURVED, DD, RPT, NA><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u,
+                                                                  tiles_v);
     e = cudaGetLastError();
     if (xZ) {
         const cudaError_t ef = workspace_free(xZ, st);
@@ -730,9 +731,14 @@ cudaError_t fp_fwd_circ(const CtGrid &g, const CtView *views, const TIn *src, vo
                         int batch, cudaStream_t st) {
     // every transaxial footprint spans at most 4 cells when its half width
     // (bounded per view on the host) is at most 1.5 cells
-    if ((DD ? g.max_m_dd_u : g.max_m_sf_u) <= 1.5f) {
-        if (g.nv >= 64) return fp_fwd_stream<TIn, CURVED, DD, 8>(g, views, src, out, out_t, batch, st);
-        return fp_fwd_stream<TIn, CURVED, DD, 1>(g, views, src, out, out_t, batch, st);
+    const float mu = DD ? g.max_m_dd_u : g.max_m_sf_u;
+    if (mu <= 1.5f) {
+        if (g.nv >= 64) return fp_fwd_stream<TIn, CURVED, DD, 8, 4>(g, views, src, out, out_t, batch, st);
+        return fp_fwd_stream<TIn, CURVED, DD, 1, 4>(g, views, src, out, out_t, batch, st);
+    }
+    if (mu <= 3.5f) {  // up to 8 cells
+        if (g.nv >= 64) return fp_fwd_stream<TIn, CURVED, DD, 8, 8>(g, views, src, out, out_t, batch, st);
+        return fp_fwd_stream<TIn, CURVED, DD, 1, 8>(g, views, src, out, out_t, batch, st);
     }
     const int tiles_u = (g.nu + 31) / 32;
     dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
