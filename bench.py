@@ -229,6 +229,13 @@ def run_suite(args):
     for name, spec, projs, dtypes in cases:
         if args.suite_filter and args.suite_filter not in name:
             continue
+        if args.suite_n:  # a smaller copy of the same field of view (profiling captures)
+            spec = W.scaled(spec, args.suite_n, args.suite_views or spec.nview)
+            name += f" scaled to {spec.nx}x{spec.ny}x{spec.nz}, {spec.nview} views, {spec.nu}x{spec.nv}"
+        if args.suite_proj:
+            projs = [p for p in projs if p == args.suite_proj]
+        if args.suite_dtype:
+            dtypes = [t for t in dtypes if t == args.suite_dtype]
         g = ct.Geometry.from_spec(spec)
         for tname in dtypes:
             x = W.phantom(spec, seed=0, device="cuda", dtype=dt[tname])
@@ -298,6 +305,10 @@ def main():
     ap.add_argument("--suite", action="store_true", help="time every projector on each workload")
     ap.add_argument("--suite-reps", type=int, default=2)
     ap.add_argument("--suite-filter", default="", help="only workloads whose name contains this")
+    ap.add_argument("--suite-n", type=int, default=0, help="scale each suite workload to n voxels per side")
+    ap.add_argument("--suite-views", type=int, default=0, help="view count of a scaled suite workload")
+    ap.add_argument("--suite-proj", default="", help="only this projector")
+    ap.add_argument("--suite-dtype", default="", help="only this storage type")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -247,9 +247,11 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
     G.beta = 0.f;
     G.max_m_sf_u = 0.f;
     G.max_m_dd_u = 0.f;
+    G.max_m_sf_v = 0.f;
     for (const CtView &V : g->host_views) {
         G.max_m_sf_u = std::max(G.max_m_sf_u, V.m_sf_u);
         G.max_m_dd_u = std::max(G.max_m_dd_u, V.m_dd_u);
+        G.max_m_sf_v = std::max(G.max_m_sf_v, V.m_sf_v);
     }
 
     if (cudaGetDevice(&g->device) != cudaSuccess) {

@@ -313,6 +313,48 @@ __device__ __forceinline__ bool slab_search(const CtView &V, const SlabCoef &c, 
     return search_circ<CURVED>(V, c, s, Flo, Fhi, Glo, Ghi, nlat, nk, l0, l1, k0, k1);
 }
 
+// ---------------------------------------------------------------- voxel-driven
+// Voxel-driven amplitude (Peters 1981, cited in Sec. 2.3): the voxel's mass
+// spread over the local ray density,
+//   3D  A = dx dy dz r D^2 / (rho^3 du dv)      2D  A = dx dy r D / (rho^2 du)
+// with r = |X - s| and rho the depth (flat) or distance from the source axis
+// (curved).
+__device__ __forceinline__ float vx_amp(const CtGrid &g, const CtView &V, float r, float den) {
+    if (g.is2d) return (g.dx * g.dy / g.du) * r * V.D / (den * den);
+    const float q = V.D / den;
+    return (g.dx * g.dy * g.dz / (g.du * g.dv)) * (r / den) * q * q;
+}
+
+// circular geometry: column quantities shared down z
+struct VxCol {
+    float fu;         // fractional u of the column (all z)
+    float sv, fv0;    // fv of voxel k: sv * k + fv0
+    float rxy2, den;  // w_x^2 + w_y^2 and the depth rho
+    float amp1;       // amplitude per unit r: A = amp1 r
+};
+
+template <bool CURVED>
+__device__ __forceinline__ VxCol vx_col(const CtView &V, const CtGrid &g, int i, int j) {
+    const float fi = (float)i, fj = (float)j;
+    const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
+    const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, V.an[3]));
+    VxCol C;
+    C.fu = Det<CURVED>::fu(V, cu, cn);
+    C.den = Det<CURVED>::den(cu, cn);
+    C.sv = V.Kv * V.av[2] / C.den;
+    C.fv0 = fmaf(V.Kv, V.av[3] / C.den, V.Cv);
+    const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
+    C.rxy2 = fmaf(wx, wx, wy * wy);
+    C.amp1 = vx_amp(g, V, 1.f, C.den);
+    return C;
+}
+
+__device__ __forceinline__ float vx_amp_col(const VxCol &C, const CtGrid &g, const CtView &V, int k) {
+    const float wz = fmaf((float)k, g.dz, V.o[2]);
+    const float t = fmaf(wz, wz, C.rxy2);
+    return C.amp1 * (t * rsqrtf(t));
+}
+
 // rounding guard added to every search window (cells)
 constexpr float kSearchPad = 2e-3f;
 

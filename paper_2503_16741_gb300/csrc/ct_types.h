@@ -46,6 +46,7 @@ struct CtGrid {
     int variant;       // GeoVariant
     float max_m_sf_u;  // largest per-view SF transaxial footprint bound (cells)
     float max_m_dd_u;  // largest per-view DD boundary bound (cells)
+    float max_m_sf_v;  // largest per-view axial half-height bound (rows)
     float alpha, beta; // output epilogue: out = alpha * result + beta * out
 };
 

@@ -11,7 +11,9 @@
 // of its central ray through one slab -- applied once per cell after the
 // gather in the forward, and to the sinogram before the gather in the back.
 // Forward and back are gather kernels (no atomics) that evaluate the same
-// per-voxel weight functions, so they form a matched pair.
+// per-voxel weight functions, so they form a matched pair.  The streaming
+// forward also serves the voxel-driven projector in circular geometry (its
+// hat weights in place of the footprints; the back kernel is in k_voxel.cu).
 #include <algorithm>
 
 #include "ct_device.cuh"
@@ -351,7 +353,55 @@ template <int RPT, int NA> struct SfFwdSmem {
     int L0[kSlabSeg], cnt[kSlabSeg], off[kSlabSeg + 1];
 };
 
-template <typename TIn, bool CURVED, bool DD, int RPT, int NA>
+// Voxel-driven stage 1 of the streaming forward: the column's centre splits
+// between cells floor(fu), floor(fu) + 1 with hat weights, and each voxel's
+// centre between rows floor(fv), floor(fv) + 1; Z accumulates amp x hat x.
+template <typename TIn, bool CURVED, int BV, int NA>
+__device__ __forceinline__ void vx_stage1(const CtView &V, const CtGrid &g, int i, int j, int B0, int bt,
+                                          const TIn *__restrict__ x, const TIn *__restrict__ volZ,
+                                          float (&Z)[BV][kItems], float (&Fu)[NA][kItems], int *a0, int tid) {
+    const VxCol C = vx_col<CURVED>(V, g, i, j);
+    const float af = floorf(C.fu), ta = C.fu - af;
+    Fu[0][tid] = 1.f - ta;
+    Fu[1][tid] = ta;
+#pragma unroll
+    for (int r = 2; r < NA; ++r) Fu[r][tid] = 0.f;
+    a0[tid] = (int)af;
+#pragma unroll
+    for (int r = 0; r < BV; ++r) Z[r][tid] = 0.f;
+    // voxels whose centre projects within one row of the tile
+    const float hw = 1.f + kSearchPad;
+    const float rsv = 1.f / C.sv;
+    const float ka = ((float)B0 - C.fv0 - hw) * rsv;
+    const float kb = ((float)(B0 + BV - 1) - C.fv0 + hw) * rsv;
+    const int k0 = max(0, (int)ceilf(fminf(ka, kb)));
+    const int k1 = min(g.nz - 1, (int)floorf(fmaxf(ka, kb)));
+    auto tap = [&](int k, float xv) {
+        const float fv = fmaf(C.sv, (float)k, C.fv0);
+        const float bf = floorf(fv), tb = fv - bf;
+        const float val = vx_amp_col(C, g, V, k) * xv;
+        const int r0 = (int)bf - B0;
+        if (r0 >= 0 && r0 < BV) Z[r0][tid] = fmaf(1.f - tb, val, Z[r0][tid]);
+        if (r0 + 1 >= 0 && r0 + 1 < BV) Z[r0 + 1][tid] = fmaf(tb, val, Z[r0 + 1][tid]);
+    };
+    if (volZ != nullptr) {  // contiguous column of the z-major copy, 4 voxels per load
+        const TIn *cz = volZ + (size_t)bt * g.nx * g.ny * g.nz + ((size_t)j * g.nx + i) * g.nz;
+        for (int kq = k0 & ~3; kq <= k1; kq += 4) {
+            float xv[4];
+            ld4(cz + kq, xv);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (kq + t >= k0 && kq + t <= k1) tap(kq + t, xv[t]);
+        }
+    } else {
+        const TIn *xc = x + (size_t)j * g.nx + i;
+        const size_t zs = (size_t)g.nx * g.ny;
+#pragma unroll 4
+        for (int k = k0; k <= k1; ++k) tap(k, ld(xc, (size_t)k * zs));
+    }
+}
+
+template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false>
 __global__ void __launch_bounds__(256, 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
             const TIn *__restrict__ volZ, void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
@@ -369,7 +419,9 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
     const CtView &V = views[v];
     const int main_y = V.main_y;
     const SlabCoef sc = slab_coef(V, main_y);
-    const float mu = (DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
+    // search half widths: footprint bound + half a cell, or the hat's one cell
+    const float mu = VOX ? 1.f + kSearchPad : (DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad;
+    const float mv = VOX ? 1.f + kSearchPad : V.m_sf_v + 0.5f + kSearchPad;
     const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
     const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
     const float T1 = Det<CURVED>::ratio_at(V, a - mu), T2 = Det<CURVED>::ratio_at(V, a + mu);
@@ -409,6 +461,9 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 const int s = seg + lo;
                 const int l = S.L0[lo] + (q - S.off[lo]);
                 const int i = main_y ? l : s, j = main_y ? s : l;
+                if constexpr (VOX) {
+                    vx_stage1<TIn, CURVED, BV, NA>(V, g, i, j, B0, bt, x, volZ, S.Z, S.Fu, S.a0, tid);
+                } else {
                 const SfCol C = sf_col<CURVED, DD>(V, g, i, j);
                 int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
                 float Fu[NA];
@@ -482,6 +537,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                                 S.Z[r][tid] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[r][tid]);
                         }
                     }
+                }
                 }
             }
             __syncthreads();
@@ -692,12 +748,12 @@ to_zmajor(const T *__restrict__ x, T *__restrict__ xZ, int nx, int ny, int nz) {
 namespace {
 constexpr int kZT = 16;
 
-template <typename TIn, bool CURVED, bool DD, int RPT, int NA>
+template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false>
 cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                           int batch, cudaStream_t st) {
     const int tiles_u = (g.nu + 31) / 32, tiles_v = (g.nv + 8 * RPT - 1) / (8 * RPT);
     const size_t smem = sizeof(SfFwdSmem<RPT, NA>);
-    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT, NA>,
+    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT, NA, VOX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a z-major copy of the volume (pooled workspace) makes every column walk
@@ -715,7 +771,7 @@ cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, 
         }
     }
     dim3 blk(32, 8), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
-    sf_fwd_circ<TIn, CURVED, DD, RPT, NA><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u,
+    sf_fwd_circ<TIn, CURVED, DD, RPT, NA, VOX><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u,
                                                                   tiles_v);
     e = cudaGetLastError();
     if (xZ) {
@@ -806,6 +862,22 @@ cudaError_t dd_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
     const cudaError_t ef = workspace_free(yp, st);
     return e != cudaSuccess ? e : ef;
 }
+
+// DD back in non-circular geometry: the same scaling, then the footprint gather
+template <typename TIn>
+cudaError_t dd_nc_back(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
+                       cudaStream_t st) {
+    const size_t n = (size_t)g.nview * g.nv * g.nu * batch;
+    float *yp = nullptr;
+    cudaError_t e = workspace_alloc((void **)&yp, n * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152u * 64u);
+    dd_prescale<TIn, false><<<blocks, 256, 0, st>>>(g, views, static_cast<const TIn *>(in), yp, batch);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_nc(1, 1, g, views, 0, yp, out_t, out, batch, st);
+    const cudaError_t ef = workspace_free(yp, st);
+    return e != cudaSuccess ? e : ef;
+}
 }  // namespace
 
 // DD backprojection in circular geometry into caller-provided scratch of at
@@ -837,8 +909,33 @@ cudaError_t launch_dd_back_scratch(const CtGrid &g, const CtView *views, int in_
                   : fp_back_circ<float, false, true>(g, views, scratch, out, out_t, batch, st);
 }
 
+namespace {
+template <typename TIn>
+cudaError_t vx_fwd_t(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
+                     cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    const bool curved = g.variant == GEO_CIRC_CURVED;
+    if (g.nv >= 64)
+        return curved ? fp_fwd_stream<TIn, true, false, 8, 2, true>(g, views, src, out, out_t, batch, st)
+                      : fp_fwd_stream<TIn, false, false, 8, 2, true>(g, views, src, out, out_t, batch, st);
+    return curved ? fp_fwd_stream<TIn, true, false, 1, 2, true>(g, views, src, out, out_t, batch, st)
+                  : fp_fwd_stream<TIn, false, false, 1, 2, true>(g, views, src, out, out_t, batch, st);
+}
+}  // namespace
+
+cudaError_t launch_vx_fwd_circ(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                               void *out, int batch, cudaStream_t st) {
+    switch (in_t) {
+    case 0: return vx_fwd_t<float>(g, views, in, out, out_t, batch, st);
+    case 1: return vx_fwd_t<__half>(g, views, in, out, out_t, batch, st);
+    default: return vx_fwd_t<__nv_bfloat16>(g, views, in, out, out_t, batch, st);
+    }
+}
+
 cudaError_t launch_sf(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st) {
+    if (g.variant == GEO_NONCIRC_FLAT && nc_footprint_fits(g, 0))
+        return launch_nc(0, dir, g, views, in_t, in, out_t, out, batch, st);
     switch (in_t) {
     case 0: return sf_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
     case 1: return sf_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);
@@ -848,7 +945,15 @@ cudaError_t launch_sf(int dir, const CtGrid &g, const CtView *views, int in_t, c
 
 cudaError_t launch_dd(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st) {
-    if (g.variant == GEO_NONCIRC_FLAT) return launch_dd_nc(dir, g, views, in_t, in, out_t, out, batch, st);
+    if (g.variant == GEO_NONCIRC_FLAT) {
+        if (!nc_footprint_fits(g, 1)) return launch_dd_nc(dir, g, views, in_t, in, out_t, out, batch, st);
+        if (dir == 0) return launch_nc(1, 0, g, views, in_t, in, out_t, out, batch, st);
+        switch (in_t) {
+        case 0: return dd_nc_back<float>(g, views, in, out, out_t, batch, st);
+        case 1: return dd_nc_back<__half>(g, views, in, out, out_t, batch, st);
+        default: return dd_nc_back<__nv_bfloat16>(g, views, in, out, out_t, batch, st);
+        }
+    }
     switch (in_t) {
     case 0: return dd_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
     case 1: return dd_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);

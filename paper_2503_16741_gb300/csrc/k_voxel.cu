@@ -6,44 +6,12 @@
 // with r = |X - s|, rho = (X - s).n (flat) or the distance of X from the
 // source axis (curved), D = source-detector distance (radius if curved).
 // The back kernel is the classic voxel-driven backprojector; the forward
-// kernel is its exact adjoint in gather form.
+// kernels are its exact adjoint in gather form: the streaming forward of
+// k_sf.cu in circular geometry, vx_fwd_nc below in non-circular geometry.
 #include "ct_device.cuh"
 #include "ct_launch.h"
 
 namespace ctp {
-
-// circular geometry: column quantities shared down z
-struct VxCol {
-    float fu;         // fractional u of the column (all z)
-    float sv, fv0;    // fv of voxel k: sv * k + fv0
-    float rxy2, den;  // w_x^2 + w_y^2 and the depth rho
-};
-
-template <bool CURVED>
-__device__ __forceinline__ VxCol vx_col(const CtView &V, const CtGrid &g, int i, int j) {
-    const float fi = (float)i, fj = (float)j;
-    const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
-    const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, V.an[3]));
-    VxCol C;
-    C.fu = Det<CURVED>::fu(V, cu, cn);
-    C.den = Det<CURVED>::den(cu, cn);
-    C.sv = V.Kv * V.av[2] / C.den;
-    C.fv0 = fmaf(V.Kv, V.av[3] / C.den, V.Cv);
-    const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
-    C.rxy2 = fmaf(wx, wx, wy * wy);
-    return C;
-}
-
-__device__ __forceinline__ float vx_amp(const CtGrid &g, const CtView &V, float r, float den) {
-    if (g.is2d) return (g.dx * g.dy / g.du) * r * V.D / (den * den);
-    const float q = V.D / den;
-    return (g.dx * g.dy * g.dz / (g.du * g.dv)) * (r / den) * q * q;
-}
-
-__device__ __forceinline__ float vx_amp_col(const VxCol &C, const CtGrid &g, const CtView &V, int k) {
-    const float wz = fmaf((float)k, g.dz, V.o[2]);
-    return vx_amp(g, V, sqrtf(fmaf(wz, wz, C.rxy2)), C.den);
-}
 
 // non-circular: per voxel
 struct VxVox {
@@ -167,12 +135,13 @@ vx_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 }
 
 // ------------------------------------------------------------ forward (gather)
-// Cell (a, b) receives voxels whose centre projects within one cell of it.
-template <typename TIn, int VARIANT>
+// Non-circular geometry: cell (a, b) receives the voxels whose centre
+// projects within one cell of it (circular geometries take the streaming
+// forward of k_sf.cu, which shares each column's u position down z).
+template <typename TIn>
 __global__ void __launch_bounds__(256)
-vx_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
-       void *__restrict__ sino, int out_t, int tiles_u) {
-    constexpr bool CURVED = VARIANT == GEO_CIRC_CURVED;
+vx_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
+          void *__restrict__ sino, int out_t, int tiles_u) {
     int bx = blockIdx.x;
     const int tu = bx % tiles_u; bx /= tiles_u;
     const int v = bx % g.nview;
@@ -189,29 +158,14 @@ vx_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
     float acc = 0.f;
     for (int s = 0; s < nslab; ++s) {
         int l0, l1, k0, k1;
-        const bool hit = VARIANT == GEO_NONCIRC_FLAT
-                             ? search_flat(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1)
-                             : slab_search<CURVED>(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1);
-        if (!hit) continue;
+        if (!search_flat(V, sc, s, a - m, a + m, b - m, b + m, nlat, g.nz, l0, l1, k0, k1)) continue;
         for (int l = l0; l <= l1; ++l) {
             const int i = main_y ? l : s, j = main_y ? s : l;
-            if (VARIANT == GEO_NONCIRC_FLAT) {
-                for (int k = k0; k <= k1; ++k) {
-                    const VxVox P = vx_vox_nc(V, g, i, j, k);
-                    const float w = hat(P.fu, a) * hat(P.fv, b);
-                    if (w == 0.f) continue;
-                    acc = fmaf(P.amp * w, ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
-                }
-            } else {
-                const VxCol C = vx_col<CURVED>(V, g, i, j);
-                const float wa = hat(C.fu, a);
-                if (wa == 0.f) continue;
-                for (int k = k0; k <= k1; ++k) {
-                    const float wb = hat(fmaf(C.sv, (float)k, C.fv0), b);
-                    if (wb == 0.f) continue;
-                    acc = fmaf(vx_amp_col(C, g, V, k) * wa * wb,
-                               ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
-                }
+            for (int k = k0; k <= k1; ++k) {
+                const VxVox P = vx_vox_nc(V, g, i, j, k);
+                const float w = hat(P.fu, a) * hat(P.fv, b);
+                if (w == 0.f) continue;
+                acc = fmaf(P.amp * w, ld(x, ((size_t)k * g.ny + j) * g.nx + i), acc);
             }
         }
     }
@@ -229,12 +183,7 @@ cudaError_t vx_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
     if (dir == 0) {
         const int tiles_u = (g.nu + 31) / 32;
         dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
-        if (g.variant == GEO_NONCIRC_FLAT)
-            vx_fwd<TIn, GEO_NONCIRC_FLAT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-        else if (g.variant == GEO_CIRC_CURVED)
-            vx_fwd<TIn, GEO_CIRC_CURVED><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
-        else
-            vx_fwd<TIn, GEO_CIRC_FLAT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
+        vx_fwd_nc<TIn><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
     } else {
         const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
         dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
@@ -251,6 +200,8 @@ cudaError_t vx_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
 
 cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                          int out_t, void *out, int batch, cudaStream_t st) {
+    if (dir == 0 && g.variant != GEO_NONCIRC_FLAT)
+        return launch_vx_fwd_circ(g, views, in_t, in, out_t, out, batch, st);
     switch (in_t) {
     case 0: return vx_launch_t<float>(dir, g, views, in, out, out_t, batch, st);
     case 1: return vx_launch_t<__half>(dir, g, views, in, out, out_t, batch, st);

@@ -128,3 +128,38 @@ def test_volume_outside_detector_gives_zero(ct):
     for proj in PROJECTORS:
         assert float(ct.forward(g, x, proj).abs().max()) == 0.0
         assert float(ct.back(g, torch.ones((3, 16, 16), device="cuda"), proj).abs().max()) == 0.0
+
+
+def _noncirc_regime(regime):
+    """Non-circular geometries whose footprints take each kernel variant
+    (the ragged geometry itself takes 4 cells x 3 rows):
+    'rows4'  -- axial half height in (1, 1.5] rows, two 64-row tiles;
+    'cells6' -- transaxial half width in (1.5, 2.5] cells;
+    'cells8' -- transaxial half width in (2.5, 3.5] cells;
+    'wide'   -- transaxial half width above 3.5 cells (the general kernels)."""
+    import dataclasses
+    spec = ragged("noncirc3d", "flat", seed=7)
+    if regime == "rows4":
+        return dataclasses.replace(spec, nv=75, dv=1.1)
+    if regime == "cells6":
+        return dataclasses.replace(spec, nu=100, du=1.3)
+    if regime == "cells8":
+        return dataclasses.replace(spec, nu=150, du=0.9)
+    return dataclasses.replace(spec, nu=220, du=0.6)
+
+
+@pytest.mark.parametrize("proj", ["sf", "dd"])
+@pytest.mark.parametrize("regime", ["rows4", "cells6", "cells8", "wide"])
+def test_noncirc_footprint_regimes(ct, regime, proj):
+    spec = _noncirc_regime(regime)
+    g = _gpu(ct, spec)
+    x = W.phantom(spec, seed=3)
+    ref = oracle.forward(spec, proj, x)
+    y = ct.forward(g, torch.as_tensor(x, dtype=torch.float32).cuda(), proj)
+    err = rel_l2(y.cpu().numpy().reshape(ref.shape), ref)
+    assert err <= TOL_F32, f"{regime}/{proj} forward: rel L2 {err:.3e}"
+    s = W.random_sino(spec, seed=4)[0]
+    refb = oracle.back(spec, proj, s)
+    xb = ct.back(g, torch.as_tensor(s.reshape(ct_sino_shape(spec)), dtype=torch.float32).cuda(), proj)
+    err = rel_l2(xb.cpu().numpy().reshape(refb.shape), refb)
+    assert err <= TOL_F32, f"{regime}/{proj} back: rel L2 {err:.3e}"
