@@ -31,6 +31,10 @@ cudaError_t launch_ray(int dir, const CtGrid &g, const CtView *views, int in_t, 
 cudaError_t launch_dd_back_scratch(const CtGrid &g, const CtView *views, int in_t, const void *in,
                                    int out_t, void *out, int batch, float *scratch, cudaStream_t st);
 
+// xZ[b][j][i][k] = x[b][k][j][i] for elements of elem_bytes (2 or 4) bytes
+cudaError_t zmajor_copy(int elem_bytes, const void *x, void *xZ, int nx, int ny, int nz, int batch,
+                        cudaStream_t st);
+
 // Stream-ordered scratch from a library-owned pool on the current device
 // (memory is kept in the pool between calls, so steady-state calls do not
 // reach the driver's allocator).

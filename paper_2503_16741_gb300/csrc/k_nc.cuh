@@ -1,0 +1,154 @@
+// k_nc.cuh -- SF-TR and DD footprint projectors in non-circular geometry
+// (flat detector with per-view tilt and in-plane rotation, Sec. 2.2), where a
+// voxel's transaxial footprint changes with its z (the footprint methods cited
+// in Sec. 2.3: Long, Fessler & Balter 2010; De Man & Basu 2004).  Every voxel
+// carries its own footprint of at most NA cells by NB rows (NA = 4, 6 or 8,
+// NB = 3 or 4, chosen by the launcher from the per-view footprint bounds;
+// wider footprints go to the general kernels).
+//   back:    thread = voxel column over a z-chunk, all views (records staged
+//            in shared memory); per voxel and view the footprint, then its
+//            NA x NB taps.
+//   forward: CTA = 64 cells x 64 rows of one view.  Per slab of the view's
+//            main axis the CTA computes, once, the footprint of every voxel
+//            that can reach its tile into shared memory (a footprint cache);
+//            each thread then gathers, for its 4 cells x 4 rows, the cached
+//            weights of the voxels in its own search box.
+// Both are gathers with a fixed summation order: deterministic, no atomics.
+// DD multiplies by the cell's path length after the forward gather; its back
+// direction takes a sinogram already scaled by it.
+// This header holds the per-voxel footprint both directions evaluate and the
+// dispatch over footprint sizes; the kernels are in k_nc_fwd.cu and
+// k_nc_back.cu.
+#pragma once
+#include "ct_device.cuh"
+#include "ct_launch.h"
+
+namespace ctp {
+
+
+template <int NA, int NB> struct NcFp {
+    int a0, b0;    // first cell, first row of the footprint
+    float Fu[NA];  // transaxial weights of cells a0 .. a0 + NA - 1
+    float Fv[NB];  // axial weights of rows b0 .. b0 + NB - 1
+    float amp;     // SF amplitude dx |w| / max(|w_x|, |w_y|); DD: 1
+};
+
+// Footprint of voxel (i, j, k) in view V.  The centre is projected with a
+// correctly rounded reciprocal; corner and end-point offsets are formed from
+// small differences, Ku (du - r dn) / (cn + dn) with r = cu / cn, where a fast
+// division's few ulp are ~1e-7 cell.
+// Trapezoid with the ramp factors formed by a fast reciprocal (relative
+// error ~1e-7 on a ramp's slope).
+__device__ __forceinline__ Trap nc_trap(float k0, float k1, float k2, float k3) {
+    return Trap{k0, k1, k2, k3, __fdividef(0.5f, fmaxf(k1 - k0, 1e-30f)), __fdividef(0.5f, fmaxf(k3 - k2, 1e-30f))};
+}
+
+template <bool DD, int NA, int NB>
+__device__ __forceinline__ void nc_fp(const CtView &V, const CtGrid &g, int i, int j, int k, NcFp<NA, NB> &P) {
+    const float fi = (float)i, fj = (float)j, fk = (float)k;
+    const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, fmaf(V.au[2], fk, V.au[3])));
+    const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, fmaf(V.an[2], fk, V.an[3])));
+    const float cv = fmaf(V.av[0], fi, fmaf(V.av[1], fj, fmaf(V.av[2], fk, V.av[3])));
+    const float rcn = __frcp_rn(cn);
+    const float r = cu * rcn, rv = cv * rcn;
+    int aref, bref;
+    float fr, vr;
+    split_cell(fmaf(V.Ku, r, V.Cu), aref, fr);
+    split_cell(fmaf(V.Kv, rv, V.Cv), bref, vr);
+    Trap T;
+    if (DD) {  // boundary points +- half a voxel along the lateral axis
+        const int q = V.main_y ? 0 : 1;
+        const float hu = 0.5f * V.au[q], hn = 0.5f * V.an[q];
+        const float e1 = fr + V.Ku * __fdividef(fmaf(r, hn, -hu), cn - hn);
+        const float e2 = fr + V.Ku * __fdividef(fmaf(-r, hn, hu), cn + hn);
+        const float lo = fminf(e1, e2), hi = fmaxf(e1, e2);
+        T = nc_trap(lo, lo, hi, hi);
+    } else {  // the four transaxial corners, sorted into a trapezoid
+        const float hxu = 0.5f * V.au[0], hxn = 0.5f * V.an[0];
+        const float hyu = 0.5f * V.au[1], hyn = 0.5f * V.an[1];
+        float t0 = fr + V.Ku * __fdividef(fmaf(-r, -hxn - hyn, -hxu - hyu), cn - hxn - hyn);
+        float t1 = fr + V.Ku * __fdividef(fmaf(-r, hxn - hyn, hxu - hyu), cn + hxn - hyn);
+        float t2 = fr + V.Ku * __fdividef(fmaf(-r, hyn - hxn, hyu - hxu), cn - hxn + hyn);
+        float t3 = fr + V.Ku * __fdividef(fmaf(-r, hxn + hyn, hxu + hyu), cn + hxn + hyn);
+        sort4(t0, t1, t2, t3);
+        T = nc_trap(t0, t1, t2, t3);
+    }
+    const int d0 = (int)floorf(T.k0 + 0.5f), d1 = (int)floorf(T.k3 + 0.5f);
+    // cells d0 .. d1 (at most NA) from the antiderivative G at their edges:
+    // G = 0 at the first edge (left of k0) and the trapezoid's area at the
+    // last (right of k3), so only the interior edges are evaluated
+#pragma unroll
+    for (int q = 0; q < NA; ++q) P.Fu[q] = 0.f;
+    const int nlast = d1 - d0;  // index of the last cell
+    float Gp = 0.f;
+#pragma unroll
+    for (int q = 0; q < NA - 1; ++q) {
+        if (q >= nlast) break;
+        const float Gn = trap_G(T, (float)(d0 + q) + 0.5f);
+        P.Fu[q] = Gn - Gp;
+        Gp = Gn;
+    }
+    // (a footprint wider than the bound by rounding loses the cells past
+    // NA - 1, whose weight is of the order of the rounding)
+    float Glast = 0.5f * ((T.k3 - T.k0) + (T.k2 - T.k1));
+    if (nlast >= NA) Glast = trap_G(T, (float)(d0 + NA - 1) + 0.5f);
+    const int ql = min(nlast, NA - 1);
+#pragma unroll
+    for (int q = 0; q < NA; ++q)
+        if (q == ql) P.Fu[q] = Glast - Gp;
+    P.a0 = aref + d0;
+    // axial rectangle: the end points (z -+ dz/2) at the voxel's (x, y) centre
+    const float hzv = 0.5f * V.av[2], hzn = 0.5f * V.an[2];
+    const float f1 = vr + V.Kv * __fdividef(fmaf(-rv, hzn, hzv), cn + hzn);
+    const float f2 = vr + V.Kv * __fdividef(fmaf(rv, hzn, -hzv), cn - hzn);
+    const float vlo = fminf(f1, f2), vhi = fmaxf(f1, f2);
+    const int e0 = (int)floorf(vlo + 0.5f);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const float e = (float)(e0 + q);
+        P.Fv[q] = overlap(vlo, vhi, e - 0.5f, e + 0.5f);
+    }
+    P.b0 = bref + e0;
+    if (DD) {
+        P.amp = 1.f;
+    } else {
+        const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
+        const float wz = fmaf(fk, g.dz, V.o[2]);
+        const float t = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+        P.amp = __fdividef(g.dx * t * rsqrtf(t), fmaxf(fabsf(wx), fabsf(wy)));
+    }
+}
+
+// Runs Run<TIn, DD, NA, NB>::go(g, args...) for the storage type, the
+// projector and the footprint bounds of g: a trapezoid of half width m cells
+// meets at most 4 cells when m <= 1.5, 6 when m <= 2.5 and 8 when m <= 3.5;
+// an axial rectangle of half height m rows at most 3 rows when m <= 1 and 4
+// when m <= 1.5.
+template <template <typename, bool, int, int> class Run, typename TIn, bool DD, typename... A>
+cudaError_t nc_dispatch_t(const CtGrid &g, A... args) {
+    const float m = DD ? g.max_m_dd_u : g.max_m_sf_u;
+    const bool r3 = g.max_m_sf_v <= 1.0f;
+    if (m <= 1.5f) return r3 ? Run<TIn, DD, 4, 3>::go(g, args...) : Run<TIn, DD, 4, 4>::go(g, args...);
+    if (m <= 2.5f) return r3 ? Run<TIn, DD, 6, 3>::go(g, args...) : Run<TIn, DD, 6, 4>::go(g, args...);
+    return r3 ? Run<TIn, DD, 8, 3>::go(g, args...) : Run<TIn, DD, 8, 4>::go(g, args...);
+}
+
+template <template <typename, bool, int, int> class Run, typename... A>
+cudaError_t nc_dispatch(int dd, int in_t, const CtGrid &g, A... args) {
+    switch (in_t) {
+    case 0: return dd ? nc_dispatch_t<Run, float, true>(g, args...) : nc_dispatch_t<Run, float, false>(g, args...);
+    case 1:
+        return dd ? nc_dispatch_t<Run, __half, true>(g, args...) : nc_dispatch_t<Run, __half, false>(g, args...);
+    default:
+        return dd ? nc_dispatch_t<Run, __nv_bfloat16, true>(g, args...)
+                  : nc_dispatch_t<Run, __nv_bfloat16, false>(g, args...);
+    }
+}
+
+// the two directions (k_nc_fwd.cu, k_nc_back.cu)
+cudaError_t launch_nc_fwd(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                          void *out, int batch, cudaStream_t st);
+cudaError_t launch_nc_back(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                           void *out, int batch, cudaStream_t st);
+
+}  // namespace ctp

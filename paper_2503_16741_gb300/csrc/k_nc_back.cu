@@ -1,0 +1,117 @@
+// k_nc_back.cu -- backprojection of the non-circular SF-TR and DD footprint
+// projectors, and the entry for both directions (the footprint and the
+// dispatch are in k_nc.cuh).
+#include "k_nc.cuh"
+
+namespace ctp {
+
+// ------------------------------------------------------------ back (gather)
+constexpr int kNcViews = 64;
+
+template <typename TIn, bool DD, int NA, int NB, int ZT>
+__global__ void __launch_bounds__(128, 6)
+nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino, void *__restrict__ vol,
+        int out_t, int tiles_x, int nzc) {
+    __shared__ CtView sview[kNcViews];
+    int bx = blockIdx.x;
+    const int tx = bx % tiles_x; bx /= tiles_x;
+    const int kc = bx % nzc;
+    const int bt = bx / nzc;
+    const int i = tx * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const bool active = i < g.nx && j < g.ny;
+    const int kbeg = kc * ZT;
+    float acc[ZT];
+#pragma unroll
+    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    const size_t vstride = (size_t)g.nv * g.nu;
+    const TIn *ys = sino + (size_t)bt * g.nview * vstride;
+    for (int v0 = 0; v0 < g.nview; v0 += kNcViews) {
+        const int nvc = min(kNcViews, g.nview - v0);
+        __syncthreads();
+        {
+            const float4 *s4 = reinterpret_cast<const float4 *>(views + v0);
+            float4 *d4 = reinterpret_cast<float4 *>(sview);
+            constexpr int W = sizeof(CtView) / sizeof(float4);
+            for (int t = tid; t < nvc * W; t += 128) d4[t] = __ldg(s4 + t);
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int vv = 0; vv < nvc; ++vv) {
+            const CtView &V = sview[vv];
+            const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
+#pragma unroll
+            for (int kk = 0; kk < ZT; ++kk) {
+                const int k = kbeg + kk;
+                if (k < g.nz) {
+                    NcFp<NA, NB> P;
+                    nc_fp<DD, NA, NB>(V, g, i, j, k, P);
+                    // cells and rows off the detector get weight 0 and a clamped
+                    // (in-bounds) address
+                    int ac[NA];
+                    float wu[NA];
+#pragma unroll
+                    for (int c = 0; c < NA; ++c) {
+                        const int a = P.a0 + c;
+                        const bool in = a >= 0 && a < g.nu;
+                        ac[c] = in ? a : 0;
+                        wu[c] = in ? P.Fu[c] : 0.f;
+                    }
+                    float s = 0.f;
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) {
+                        const int b = P.b0 + q;
+                        if (P.Fv[q] != 0.f && b >= 0 && b < g.nv) {
+                            const TIn *row = yv + (size_t)b * g.nu;
+                            float rs = wu[0] * ld(row, (size_t)ac[0]);
+#pragma unroll
+                            for (int c = 1; c < NA; ++c) rs = fmaf(wu[c], ld(row, (size_t)ac[c]), rs);
+                            s = fmaf(P.Fv[q], rs, s);
+                        }
+                    }
+                    acc[kk] = fmaf(P.amp, s, acc[kk]);
+                }
+            }
+        }
+    }
+    if (!active) return;
+    const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
+#pragma unroll
+    for (int kk = 0; kk < ZT; ++kk) {
+        const int k = kbeg + kk;
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+    }
+}
+
+namespace {
+template <typename TIn, bool DD, int NA, int NB> struct NcBack {
+    static cudaError_t go(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
+                          cudaStream_t st) {
+        constexpr int ZT = 8;
+        const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + ZT - 1) / ZT;
+        dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+        nc_back<TIn, DD, NA, NB, ZT><<<grd, blk, 0, st>>>(g, views, static_cast<const TIn *>(in), out, out_t,
+                                                          tiles_x, nzc);
+        return cudaGetLastError();
+    }
+};
+}  // namespace
+
+cudaError_t launch_nc_back(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                           void *out, int batch, cudaStream_t st) {
+    return nc_dispatch<NcBack>(dd, in_t, g, views, in, out, out_t, batch, st);
+}
+
+bool nc_footprint_fits(const CtGrid &g, int dd) {
+    // at most 8 cells (half width <= 3.5) by 4 rows (half height <= 1.5)
+    return (dd ? g.max_m_dd_u : g.max_m_sf_u) <= 3.5f && g.max_m_sf_v <= 1.5f;
+}
+
+cudaError_t launch_nc(int dd, int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+                      int out_t, void *out, int batch, cudaStream_t st) {
+    return dir == 0 ? launch_nc_fwd(dd, g, views, in_t, in, out_t, out, batch, st)
+                    : launch_nc_back(dd, g, views, in_t, in, out_t, out, batch, st);
+}
+
+}  // namespace ctp

@@ -923,6 +923,16 @@ cudaError_t vx_fwd_t(const CtGrid &g, const CtView *views, const void *in, void 
 }
 }  // namespace
 
+cudaError_t zmajor_copy(int elem_bytes, const void *x, void *xZ, int nx, int ny, int nz, int batch,
+                        cudaStream_t st) {
+    dim3 tb(32, 8), tg((unsigned)(((nx + 31) / 32) * ((nz + 31) / 32)), (unsigned)ny, (unsigned)batch);
+    if (elem_bytes == 4)
+        to_zmajor<float><<<tg, tb, 0, st>>>(static_cast<const float *>(x), static_cast<float *>(xZ), nx, ny, nz);
+    else
+        to_zmajor<__half><<<tg, tb, 0, st>>>(static_cast<const __half *>(x), static_cast<__half *>(xZ), nx, ny, nz);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vx_fwd_circ(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                                void *out, int batch, cudaStream_t st) {
     switch (in_t) {
