@@ -41,8 +41,8 @@ N_SM, FP32_LANES = 152, 128
 # DRAM bytes per launch from one ncu capture of the same kernel source
 # (sha256 of the .cu at capture time); null once the source changes.
 NCU_TRAFFIC = {
-    "sf_back": {"bytes": 414.9e6, "src": "0a7d5f3f5e8b8e73"},
-    "sf_fwd": {"bytes": 915.1e6, "src": "0a7d5f3f5e8b8e73"},
+    "sf_back": {"bytes": 412.7e6, "src": "0cb5f824700d5929"},
+    "sf_fwd": {"bytes": 941.5e6, "src": "0cb5f824700d5929"},
 }
 
 
@@ -422,7 +422,7 @@ def main():
                          "frac": hbm_ach / hbm_peak, "bytes": "compulsory: read input once, write output once",
                          "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": e2e,
-        "gpu_launches": 2 * K,
+        "gpu_launches": 3 * K,  # per step: z-major copy, SF forward, SF back
         "clocks": clk,
     }
     if not args.no_serving:
