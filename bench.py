@@ -262,7 +262,48 @@ def run_suite(args):
                                   "fwd_ms": tf, "back_ms": tb, "fwd_gups": upd / tf / 1e6,
                                   "back_gups": upd / tb / 1e6,
                                   "pair_gups": 2 * upd / (tf + tb) / 1e6}), flush=True)
+        if "curved" in name and not args.suite_proj:
+            mbir_loop_timing(ct, g, spec)
         g.close()
+
+
+def mbir_loop_timing(ct, g, spec, steps: int = 10):
+    """The 10-step least-squares loop of the curved workload with DD: the
+    fused form (two accumulating launches per step) and the same steps taken
+    with torch.autograd through the Projector module."""
+    import torch
+    from paper_2503_16741_gb300.mbir import ls_gradient_descent, ls_step_size
+    import workloads as W
+    x_true = W.phantom(spec, seed=0, device="cuda", dtype=torch.float32).reshape(g.vol_shape)
+    y = ct.forward(g, x_true, "dd")
+    lr = ls_step_size(g, "dd")
+    A = ct.Projector(g, "proj", "DD", "forward")
+
+    def autograd_loop():
+        x = torch.zeros(g.vol_shape, device="cuda", requires_grad=True)
+        for _ in range(steps):
+            loss = 0.5 * ((A(x) - y) ** 2).sum()
+            (gr,) = torch.autograd.grad(loss, [x])
+            x.data -= lr * gr
+        return x.detach()
+
+    out = {}
+    for label, fn in (("fused", lambda: ls_gradient_descent(g, y, "dd", steps, lr=lr)),
+                      ("autograd", autograd_loop)):
+        fn()
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        x = fn()
+        e[1].record()
+        torch.cuda.synchronize()
+        ms = e[0].elapsed_time(e[1])
+        res = float(((ct.forward(g, x, "dd") - y).double() ** 2).sum() / (y.double() ** 2).sum())
+        out[label] = {"ms": ms, "ms_per_step": ms / steps, "rel_residual": res}
+    upd = 2 * steps * spec.n_vox * spec.nview
+    print(json.dumps({"suite": "10-step least-squares loop, DD, curved 512^2x128 / 984 views",
+                      "fused": out["fused"], "autograd": out["autograd"],
+                      "fused_gups": upd / out["fused"]["ms"] / 1e6}), flush=True)
 
 
 def run_reference(args):

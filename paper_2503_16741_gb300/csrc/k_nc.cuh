@@ -28,6 +28,7 @@ namespace ctp {
 
 template <int NA, int NB> struct NcFp {
     int a0, b0;    // first cell, first row of the footprint
+    int n;         // cells with a weight (at most NA)
     float Fu[NA];  // transaxial weights of cells a0 .. a0 + NA - 1
     float Fv[NB];  // axial weights of rows b0 .. b0 + NB - 1
     float amp;     // SF amplitude dx |w| / max(|w_x|, |w_y|); DD: 1
@@ -93,6 +94,7 @@ __device__ __forceinline__ void nc_fp(const CtView &V, const CtGrid &g, int i, i
     float Glast = 0.5f * ((T.k3 - T.k0) + (T.k2 - T.k1));
     if (nlast >= NA) Glast = trap_G(T, (float)(d0 + NA - 1) + 0.5f);
     const int ql = min(nlast, NA - 1);
+    P.n = ql + 1;
 #pragma unroll
     for (int q = 0; q < NA; ++q)
         if (q == ql) P.Fu[q] = Glast - Gp;

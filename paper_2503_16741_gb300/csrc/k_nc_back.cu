@@ -6,13 +6,20 @@
 namespace ctp {
 
 // ------------------------------------------------------------ back (gather)
-constexpr int kNcViews = 64;
+// Views staged per round: few enough that the sinogram rows a warp reads
+// for them stay in L1 while the thread runs over its voxels.
+constexpr int kNcViews = 16;
 
+// Thread = voxel column (i, j) over ZT voxels; per round of views the thread
+// runs over its voxels one at a time (the per-voxel body appears once in the
+// code, which keeps the kernel within the instruction cache) with the
+// voxel's sum carried in shared memory between rounds.
 template <typename TIn, bool DD, int NA, int NB, int ZT>
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(128, 8)
 nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino, void *__restrict__ vol,
         int out_t, int tiles_x, int nzc) {
     __shared__ CtView sview[kNcViews];
+    __shared__ float acc[ZT][128];
     int bx = blockIdx.x;
     const int tx = bx % tiles_x; bx /= tiles_x;
     const int kc = bx % nzc;
@@ -22,9 +29,8 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const bool active = i < g.nx && j < g.ny;
     const int kbeg = kc * ZT;
-    float acc[ZT];
 #pragma unroll
-    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    for (int q = 0; q < ZT; ++q) acc[q][tid] = 0.f;
     const size_t vstride = (size_t)g.nv * g.nu;
     const TIn *ys = sino + (size_t)bt * g.nview * vstride;
     for (int v0 = 0; v0 < g.nview; v0 += kNcViews) {
@@ -38,41 +44,45 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
         }
         __syncthreads();
         if (!active) continue;
-        for (int vv = 0; vv < nvc; ++vv) {
-            const CtView &V = sview[vv];
-            const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
+#pragma unroll 1
+        for (int kk = 0; kk < ZT; ++kk) {
+            const int k = kbeg + kk;
+            if (k >= g.nz) break;
+            float a = acc[kk][tid];
+            for (int vv = 0; vv < nvc; ++vv) {
+                const CtView &V = sview[vv];
+                const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
+                NcFp<NA, NB> P;
+                nc_fp<DD, NA, NB>(V, g, i, j, k, P);
+                // cells off the detector get weight 0 and a clamped (in-bounds)
+                // address; cells past the footprint are not read
+                int ac[NA];
+                float wu[NA];
 #pragma unroll
-            for (int kk = 0; kk < ZT; ++kk) {
-                const int k = kbeg + kk;
-                if (k < g.nz) {
-                    NcFp<NA, NB> P;
-                    nc_fp<DD, NA, NB>(V, g, i, j, k, P);
-                    // cells and rows off the detector get weight 0 and a clamped
-                    // (in-bounds) address
-                    int ac[NA];
-                    float wu[NA];
-#pragma unroll
-                    for (int c = 0; c < NA; ++c) {
-                        const int a = P.a0 + c;
-                        const bool in = a >= 0 && a < g.nu;
-                        ac[c] = in ? a : 0;
-                        wu[c] = in ? P.Fu[c] : 0.f;
-                    }
-                    float s = 0.f;
-#pragma unroll
-                    for (int q = 0; q < NB; ++q) {
-                        const int b = P.b0 + q;
-                        if (P.Fv[q] != 0.f && b >= 0 && b < g.nv) {
-                            const TIn *row = yv + (size_t)b * g.nu;
-                            float rs = wu[0] * ld(row, (size_t)ac[0]);
-#pragma unroll
-                            for (int c = 1; c < NA; ++c) rs = fmaf(wu[c], ld(row, (size_t)ac[c]), rs);
-                            s = fmaf(P.Fv[q], rs, s);
-                        }
-                    }
-                    acc[kk] = fmaf(P.amp, s, acc[kk]);
+                for (int c = 0; c < NA; ++c) {
+                    const int ca = P.a0 + c;
+                    const bool in = ca >= 0 && ca < g.nu;
+                    ac[c] = in ? ca : 0;
+                    wu[c] = in ? P.Fu[c] : 0.f;
                 }
+                float s = 0.f;
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    const int b = P.b0 + q;
+                    if (P.Fv[q] != 0.f && b >= 0 && b < g.nv) {
+                        const TIn *row = yv + (size_t)b * g.nu;
+                        float rs = wu[0] * ld(row, (size_t)ac[0]);
+#pragma unroll
+                        for (int c = 1; c < NA; ++c) {
+                            if (c >= P.n) break;
+                            rs = fmaf(wu[c], ld(row, (size_t)ac[c]), rs);
+                        }
+                        s = fmaf(P.Fv[q], rs, s);
+                    }
+                }
+                a = fmaf(P.amp, s, a);
             }
+            acc[kk][tid] = a;
         }
     }
     if (!active) return;
@@ -80,7 +90,7 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk][tid], out_t);
     }
 }
 
