@@ -163,6 +163,9 @@ __device__ __forceinline__ float ray_weight(const CtView &V, const CtGrid &g, in
     return chord(e, dh, hh);
 }
 
+// The voxel loop of both back kernels is not unrolled (its body, with the
+// per-cell chord search, appears once in the code, which keeps the kernels
+// within the instruction cache); the voxels' sums are kept in shared memory.
 template <typename TIn, bool CURVED, int ZT>
 __global__ void __launch_bounds__(128)
 ray_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
@@ -175,9 +178,10 @@ ray_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict_
     const int j = blockIdx.y * 4 + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     const int kbeg = kc * ZT;
-    float acc[ZT];
+    __shared__ float acc_s[ZT][128];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    for (int q = 0; q < ZT; ++q) acc_s[q][tid] = 0.f;
     const float hh[3] = {0.5f * g.dx, 0.5f * g.dy, 0.5f * g.dz};
     const size_t vstride = (size_t)g.nv * g.nu;
     const TIn *ys = sino + (size_t)bt * g.nview * vstride;
@@ -215,7 +219,7 @@ ray_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict_
             dmax = cn + hd;
         }
         const TIn *yv = ys + (size_t)v * vstride;
-#pragma unroll
+#pragma unroll 1
         for (int kk = 0; kk < ZT; ++kk) {
             const int k = kbeg + kk;
             if (k >= g.nz) break;
@@ -236,14 +240,14 @@ ray_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict_
                     if (w > 0.f) s = fmaf(w, ld(row, (size_t)a), s);
                 }
             }
-            acc[kk] += s;
+            acc_s[kk][tid] += s;
         }
     }
     const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc_s[kk][tid], out_t);
     }
 }
 
@@ -259,9 +263,10 @@ ray_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
     const int j = blockIdx.y * 4 + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
     const int kbeg = kc * ZT;
-    float acc[ZT];
+    __shared__ float acc_s[ZT][128];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
 #pragma unroll
-    for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
+    for (int q = 0; q < ZT; ++q) acc_s[q][tid] = 0.f;
     const float hh[3] = {0.5f * g.dx, 0.5f * g.dy, 0.5f * g.dz};
     const size_t vstride = (size_t)g.nv * g.nu;
     const TIn *ys = sino + (size_t)bt * g.nview * vstride;
@@ -269,7 +274,7 @@ ray_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
     for (int v = 0; v < g.nview; ++v) {
         const CtView &V = views[v];
         const TIn *yv = ys + (size_t)v * vstride;
-#pragma unroll
+#pragma unroll 1
         for (int kk = 0; kk < ZT; ++kk) {
             const int k = kbeg + kk;
             if (k >= g.nz) break;
@@ -309,14 +314,14 @@ ray_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                     if (w > 0.f) s = fmaf(w, ld(row, (size_t)a), s);
                 }
             }
-            acc[kk] += s;
+            acc_s[kk][tid] += s;
         }
     }
     const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
 #pragma unroll
     for (int kk = 0; kk < ZT; ++kk) {
         const int k = kbeg + kk;
-        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc[kk], out_t);
+        if (k < g.nz) st_out(g, vol, base + (size_t)k * g.ny * g.nx, acc_s[kk][tid], out_t);
     }
 }
 
