@@ -77,9 +77,10 @@ def test_adjoint_identity_fp32(ct, kind, det, proj):
     assert abs(lhs - rhs) <= TOL_F32 * abs(lhs), f"{lhs} vs {rhs}"
 
 
+@pytest.mark.parametrize("kind", ["circ3d", "noncirc3d"])
 @pytest.mark.parametrize("proj", PROJECTORS)
-def test_batch_items_independent_and_deterministic(ct, proj):
-    spec = ragged("circ3d", "flat", seed=4)
+def test_batch_items_independent_and_deterministic(ct, proj, kind):
+    spec = ragged(kind, "flat", seed=4)
     g = _gpu(ct, spec)
     gen = torch.Generator(device="cuda").manual_seed(9)
     x = torch.rand((2, 3) + ct_vol_shape(spec), generator=gen, device="cuda")
@@ -104,10 +105,12 @@ def test_view_subset_equals_slice(ct, proj):
     assert torch.equal(sub, full[views])
 
 
-def test_degenerate_sizes(ct):
-    """Single voxel, single cell, single view."""
-    spec = W.GeometrySpec("circ3d", "flat", 1, 1, 1, 2.0, 2.0, 2.0, 1, 1, 3.0, 3.0, 1,
-                          theta=0.3, sad=100.0, sdd=200.0)
+@pytest.mark.parametrize("kind", ["circ3d", "noncirc3d"])
+def test_degenerate_sizes(ct, kind):
+    """Single voxel, single cell, single view (tilted in the non-circular case)."""
+    kw = dict(phi=0.08, psi=-0.03) if kind == "noncirc3d" else {}
+    spec = W.GeometrySpec(kind, "flat", 1, 1, 1, 2.0, 2.0, 2.0, 1, 1, 3.0, 3.0, 1,
+                          theta=0.3, sad=100.0, sdd=200.0, **kw)
     g = _gpu(ct, spec)
     for proj in PROJECTORS:
         x = torch.ones((1, 1, 1), device="cuda")
@@ -119,10 +122,12 @@ def test_degenerate_sizes(ct):
         assert rel_l2(xb.cpu().numpy(), refb) <= TOL_F32
 
 
-def test_volume_outside_detector_gives_zero(ct):
+@pytest.mark.parametrize("kind", ["circ3d", "noncirc3d"])
+def test_volume_outside_detector_gives_zero(ct, kind):
     """A detector offset so far that no ray meets the volume: all zeros."""
-    spec = W.GeometrySpec("circ3d", "flat", 8, 8, 8, 1.0, 1.0, 1.0, 16, 16, 1.0, 1.0, 3,
-                          theta=[0.0, 1.0, 2.0], sad=200.0, sdd=400.0, u_ofst=500.0)
+    kw = dict(phi=[0.05, -0.05, 0.02]) if kind == "noncirc3d" else {}
+    spec = W.GeometrySpec(kind, "flat", 8, 8, 8, 1.0, 1.0, 1.0, 16, 16, 1.0, 1.0, 3,
+                          theta=[0.0, 1.0, 2.0], sad=200.0, sdd=400.0, u_ofst=500.0, **kw)
     g = _gpu(ct, spec)
     x = torch.ones((8, 8, 8), device="cuda")
     for proj in PROJECTORS:
