@@ -74,3 +74,32 @@ def test_noncirc_512_full_size_sf(ct, dtype, bound):
     xb = ct.back(g, y, "sf")
     ref = oracle.back_voxels(spec, "sf", yy.double().cpu().numpy(), sel)
     assert rel_l2(xb.float().cpu().numpy().ravel()[sel], ref) <= bound
+
+
+def test_fan2d_small_full_size_ray_forward_voxel_back(ct):
+    """The fan-beam workload in full: ray-driven forward of the phantom and
+    voxel-driven backprojection of its sinogram, every output element."""
+    spec = W.fan2d_small()
+    x = W.phantom(spec, seed=0)
+    g = ct.Geometry.from_spec(spec)
+    y = ct.forward(g, torch.as_tensor(x.reshape(spec.ny, spec.nx), dtype=torch.float32).cuda(), "ray")
+    torch.cuda.synchronize()
+    y_ref = oracle.forward(spec, "ray", x)
+    assert rel_l2(y.cpu().numpy().reshape(y_ref.shape), y_ref) <= TOL_F32
+    xb = ct.back(g, y, "voxel")
+    xb_ref = oracle.back(spec, "voxel", y.double().cpu().numpy().reshape(y_ref.shape))
+    assert rel_l2(xb.cpu().numpy().reshape(xb_ref.shape), xb_ref) <= TOL_F32
+
+
+def test_noncirc_512_full_size_dd(ct):
+    spec = W.noncirc3d_saddle()
+    x = W.phantom(spec, seed=4)
+    g = ct.Geometry.from_spec(spec)
+    y = ct.forward(g, torch.as_tensor(x, dtype=torch.float32).cuda(), "dd")
+    torch.cuda.synchronize()
+    views = [3, 250]
+    assert rel_l2(y[views].cpu().numpy(), oracle.forward(spec.subset(views), "dd", x)) <= TOL_F32
+    sel = _sample_voxels(spec, 100, 4)
+    xb = ct.back(g, y, "dd")
+    ref = oracle.back_voxels(spec, "dd", y.double().cpu().numpy(), sel)
+    assert rel_l2(xb.cpu().numpy().ravel()[sel], ref) <= TOL_F32
