@@ -323,9 +323,25 @@ def mbir_loop_timing(ct, g, spec, steps: int = 10):
         ms = e[0].elapsed_time(e[1])
         res = float(((ct.forward(g, x, "dd") - y).double() ** 2).sum() / (y.double() ** 2).sum())
         out[label] = {"ms": ms, "ms_per_step": ms / steps, "rel_residual": res}
+    # ordered subsets: 12 interleaved subsets of 82 views, `steps` epochs
+    # (an epoch projects every view once each way, like one full step)
+    from paper_2503_16741_gb300.mbir import ordered_subsets, os_gradient_descent
+    subsets = ordered_subsets(spec.nview, 12)
+    lrs = [ls_step_size(g.subset(v), "dd") for v in subsets]
+    os_gradient_descent(g, y, "dd", 12, 1, lr=lrs)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    x = os_gradient_descent(g, y, "dd", 12, steps, lr=lrs)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1])
+    res = float(((ct.forward(g, x, "dd") - y).double() ** 2).sum() / (y.double() ** 2).sum())
+    out["ordered_subsets_12"] = {"ms": ms, "ms_per_epoch": ms / steps, "rel_residual": res}
     upd = 2 * steps * spec.n_vox * spec.nview
     print(json.dumps({"suite": "10-step least-squares loop, DD, curved 512^2x128 / 984 views",
                       "fused": out["fused"], "autograd": out["autograd"],
+                      "ordered_subsets_12": out["ordered_subsets_12"],
                       "fused_gups": upd / out["fused"]["ms"] / 1e6}), flush=True)
 
 

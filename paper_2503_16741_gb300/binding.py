@@ -128,15 +128,19 @@ class Geometry:
         d.dx, d.dy, d.dz = self.dx, self.dy, self.dz
         d.nu, d.nv, d.du, d.dv, d.nview = self.nu, self.nv, self.du, self.dv, self.nview
         self._keep = []
+        self._params = {}  # per-view parameters as given (for subset())
         for name in PER_VIEW:
             val = params.get(name, 500.0 if name == "sad" else (1000.0 if name == "sdd" else 0.0))
             arr = np.ascontiguousarray(np.atleast_1d(np.asarray(val, dtype=np.float64)).ravel())
             self._keep.append(arr)
+            self._params[name] = arr
             setattr(d, name, arr.ctypes.data_as(C.POINTER(C.c_double)))
             setattr(d, "n_" + name, int(arr.size))
+        self._poses = None
         if poses is not None:
             p = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(self.nview, 12))
             self._keep.append(p)
+            self._poses = p
             d.poses = p.ctypes.data_as(C.POINTER(C.c_double))
         else:
             d.poses = C.POINTER(C.c_double)()
@@ -151,6 +155,18 @@ class Geometry:
         return cls(spec.kind, spec.det, spec.nx, spec.ny, spec.nz, spec.dx, spec.dy, spec.dz,
                    spec.nu, spec.nv, spec.du, spec.dv, spec.nview,
                    poses=getattr(spec, "poses", None), **kw)
+
+    def subset(self, views: Sequence[int]) -> "Geometry":
+        """The same scan restricted to the listed views, in the listed order
+        (an ordered subset, Sec. 2.2: every parameter is per view): its
+        projections equal those rows of the full geometry's."""
+        views = np.asarray(views, dtype=np.int64).ravel()
+        if views.size == 0 or views.min() < 0 or views.max() >= self.nview:
+            raise ValueError(f"views must lie in [0, {self.nview})")
+        kw = {n: (a if a.size == 1 else a[views]) for n, a in self._params.items()}
+        return Geometry(self.kind, self.det, self.nx, self.ny, self.nz, self.dx, self.dy, self.dz,
+                        self.nu, self.nv, self.du, self.dv, int(views.size),
+                        poses=None if self._poses is None else self._poses[views], **kw)
 
     @property
     def handle(self) -> C.c_void_p:

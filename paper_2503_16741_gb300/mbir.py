@@ -1,14 +1,17 @@
 """Model-based iterative reconstruction by gradient descent on the
 least-squares data term (the example of Sec. 2.4, Eq. 3 without the TV term):
-x <- x - lr * A^T (A x - y).
+x <- x - lr * A^T (A x - y), over all views or over ordered subsets of them.
 
 Each step is two library calls on one stream: ct_forward_acc forms the
 residual r = A x - y in place of a copy of y, and ct_back_acc applies
 x <- x - lr A^T r in place -- no elementwise passes and no host round trip.
+Ordered subsets (OS) take the step with the views of one subset at a time
+(A_s, y_s: the subset's rows), cycling through the subsets; each subset is a
+geometry of its own (Geometry.subset).
 """
 from __future__ import annotations
 
-from typing import Optional
+from typing import List, Optional, Sequence
 
 import torch
 
@@ -51,4 +54,40 @@ def ls_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, steps: 
             r.copy_(y)
             forward_acc(geom, x, r, 1.0, -1.0, projector, stream=s)
             back_acc(geom, r, x, -lr, 1.0, projector, stream=s)
+    return x
+
+
+def ordered_subsets(nview: int, n_subsets: int) -> List[List[int]]:
+    """Interleaved view subsets: subset s holds views s, s + S, s + 2S, ...
+    (every view once; consecutive subsets are spread over the whole arc)."""
+    if not 1 <= n_subsets <= nview:
+        raise ValueError("need 1 <= n_subsets <= nview")
+    return [list(range(s, nview, n_subsets)) for s in range(n_subsets)]
+
+
+def os_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, n_subsets: int, epochs: int,
+                        lr: Optional[Sequence[float]] = None, x0: Optional[torch.Tensor] = None,
+                        stream=None, subsets: Optional[List[List[int]]] = None) -> torch.Tensor:
+    """`epochs` passes over the ordered subsets, one gradient step on
+    1/2 ||A_s x - y_s||^2 per subset s, with step lr[s] (default
+    1 / ||A_s||^2 with the same 2 % margin as ls_step_size).
+    y: (..., nview, [nv,] nu); returns x with y's batch shape and dtype."""
+    subsets = subsets if subsets is not None else ordered_subsets(geom.nview, n_subsets)
+    geoms = [geom.subset(v) for v in subsets]
+    if lr is None:
+        lr = [ls_step_size(g, projector) for g in geoms]
+    k = len(geom.sino_shape)
+    lead = y.shape[:-k]
+    s = stream if stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        idx = [torch.as_tensor(v, device=y.device) for v in subsets]
+        ys = [y.index_select(y.dim() - k, i).contiguous() for i in idx]
+        rs = [torch.empty_like(t) for t in ys]
+        x = (torch.zeros(tuple(lead) + geom.vol_shape, dtype=y.dtype, device=y.device)
+             if x0 is None else x0.clone())
+        for _ in range(epochs):
+            for g, ysub, r, step in zip(geoms, ys, rs, lr):
+                r.copy_(ysub)
+                forward_acc(g, x, r, 1.0, -1.0, projector, stream=s)
+                back_acc(g, r, x, -step, 1.0, projector, stream=s)
     return x

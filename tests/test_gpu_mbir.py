@@ -79,3 +79,55 @@ def test_ten_step_ls_loop_on_curved_geometry_matches_autograd(ct):
         (gr,) = torch.autograd.grad(loss, [x])
         x.data -= lr * gr
     assert rel_l2(fused.cpu().numpy(), x.detach().cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["circ3d", "noncirc3d"])
+def test_geometry_subset_projects_those_rows(ct, kind):
+    spec = ragged(kind, "flat", seed=40)
+    g = ct.Geometry.from_spec(spec)
+    x = torch.as_tensor(W.phantom(spec, seed=3), dtype=torch.float32).cuda()
+    views = [2, 9, 10, 21]
+    for proj in ("sf", "dd", "voxel", "ray"):
+        assert torch.equal(ct.forward(g.subset(views), x, proj), ct.forward(g, x, proj)[views])
+
+
+def test_one_ordered_subset_is_the_full_gradient_step(ct):
+    from paper_2503_16741_gb300.mbir import ls_gradient_descent, ls_step_size, os_gradient_descent
+    spec = ragged("circ3d", "flat", seed=41)
+    g = ct.Geometry.from_spec(spec)
+    y = ct.forward(g, torch.as_tensor(W.phantom(spec, seed=4), dtype=torch.float32).cuda(), "sf")
+    lr = ls_step_size(g, "sf")
+    assert torch.equal(os_gradient_descent(g, y, "sf", 1, 3, lr=[lr]), ls_gradient_descent(g, y, "sf", 3, lr=lr))
+
+
+@pytest.mark.parametrize("proj", ["sf", "dd"])
+def test_ordered_subsets_match_oracle_iteration(ct, proj):
+    """Two epochs over 3 interleaved view subsets: each step
+    x <- x - lr_s A_s^T (A_s x - y_s) against the same iteration in FP64."""
+    from paper_2503_16741_gb300.mbir import ls_step_size, ordered_subsets, os_gradient_descent
+    spec = ragged("noncirc3d", "flat", seed=42)
+    g = ct.Geometry.from_spec(spec)
+    truth = W.phantom(spec, seed=5)
+    y0 = oracle.forward(spec, proj, truth)
+    subsets = ordered_subsets(spec.nview, 3)
+    lrs = [ls_step_size(g.subset(v), proj) for v in subsets]
+    x = os_gradient_descent(g, torch.as_tensor(y0, dtype=torch.float32).cuda(), proj, 3, 2, lr=lrs)
+    xr = np.zeros_like(truth)
+    for _ in range(2):
+        for v, lr in zip(subsets, lrs):
+            sub = spec.subset(v)
+            xr = xr - lr * oracle.back(sub, proj, oracle.forward(sub, proj, xr) - y0[v])
+    assert rel_l2(x.cpu().numpy(), xr) <= 3 * TOL_F32
+
+
+def test_ordered_subsets_reduce_the_data_term_faster_per_epoch(ct):
+    """An epoch over 6 subsets costs about one full gradient step (every view
+    projected once each way) and lowers the data term further."""
+    from paper_2503_16741_gb300.mbir import ls_gradient_descent, os_gradient_descent
+    spec = ragged("circ3d", "flat", seed=43)
+    g = ct.Geometry.from_spec(spec)
+    y = ct.forward(g, torch.as_tensor(W.phantom(spec, seed=6), dtype=torch.float32).cuda(), "dd")
+    loss = lambda x: float(((ct.forward(g, x, "dd") - y).double() ** 2).sum())
+    full = ls_gradient_descent(g, y, "dd", 2)
+    osx = os_gradient_descent(g, y, "dd", 6, 2)
+    assert loss(osx) < loss(full) < loss(torch.zeros_like(full))
