@@ -249,6 +249,8 @@ def run_suite(args):
              ("circ 256^3, 360 views, 512x384", W.circ3d_256(), ["sf", "dd", "voxel", "ray"], ["f32", "f16"]),
              ("circ curved 512^2x128, 984 views, 888x64", W.circ3d_curved(), ["dd", "sf"], ["f32"]),
              ("saddle 512^3, 500 views, 1024^2", W.noncirc3d_saddle(), ["sf", "dd"], ["f32", "f16", "bf16"])]
+    if not args.suite_filter or args.suite_filter in "sinusoidal":
+        tv_adam_timing(ct)
     for name, spec, projs, dtypes in cases:
         if args.suite_filter and args.suite_filter not in name:
             continue
@@ -288,6 +290,36 @@ def run_suite(args):
         if "curved" in name and not args.suite_proj:
             mbir_loop_timing(ct, g, spec)
         g.close()
+
+
+def tv_adam_timing(ct, iters: int = 200):
+    """TV-regularised MBIR by Adam through autograd (the objective of Sec. 3)
+    on a 200-view sinusoidal trajectory (source z = 20 mm sin 2 theta),
+    128^3 volume of 1.6 mm voxels, flat 256 x 192 detector of 1.6 mm, SF."""
+    import numpy as np
+    import torch
+    from paper_2503_16741_gb300.mbir import tv_mbir_adam
+    import workloads as W
+    nview = 200
+    theta = np.linspace(0, 2 * np.pi, nview, endpoint=False)
+    spec = W.GeometrySpec("noncirc3d", "flat", 128, 128, 128, 1.6, 1.6, 1.6, 256, 192, 1.6, 1.6, nview,
+                          theta=theta, sad=785.0, sdd=1200.0, z_src=20.0 * np.sin(2 * theta))
+    g = ct.Geometry.from_spec(spec)
+    x_true = W.phantom(spec, seed=0, device="cuda", dtype=torch.float32).reshape(g.vol_shape)
+    y = ct.forward(g, x_true, "sf")
+    tv_mbir_adam(g, y, "sf", 3, 0.5, 5e-4)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    x, hist = tv_mbir_adam(g, y, "sf", iters, 0.5, 5e-4)
+    e[1].record()
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1])
+    err = float((x - x_true).double().norm() / x_true.double().norm())
+    print(json.dumps({"suite": f"TV-Adam MBIR, {iters} iterations, sinusoidal trajectory 128^3 / 200 views",
+                      "ms": ms, "ms_per_iteration": ms / iters, "objective_first_last": [hist[0], hist[-1]],
+                      "rel_error": err}), flush=True)
+    g.close()
 
 
 def mbir_loop_timing(ct, g, spec, steps: int = 10):

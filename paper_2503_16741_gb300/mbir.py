@@ -91,3 +91,40 @@ def os_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, n_subse
                 forward_acc(g, x, r, 1.0, -1.0, projector, stream=s)
                 back_acc(g, r, x, -step, 1.0, projector, stream=s)
     return x
+
+
+def total_variation(x: torch.Tensor, eps: float = 1e-4) -> torch.Tensor:
+    """Smoothed isotropic total variation of the last three (or two) axes:
+    sum sqrt(|forward differences|^2 + eps^2), zero difference past the last
+    voxel.  Written with torch operations, so autograd differentiates it."""
+    nd = 3 if x.dim() >= 3 else 2
+    sq = torch.zeros_like(x)
+    for ax in range(x.dim() - nd, x.dim()):
+        d = torch.diff(x, dim=ax, append=x.narrow(ax, x.shape[ax] - 1, 1))
+        sq = sq + d * d
+    return torch.sqrt(sq + eps * eps).sum()
+
+
+def tv_mbir_adam(geom: Geometry, y: torch.Tensor, projector: str, iters: int, lam: float, lr: float,
+                 x0: Optional[torch.Tensor] = None, eps: float = 1e-4):
+    """MBIR with the objective of Sec. 3 (Eq. 3): ||A x - y||^2 + lam TV(x),
+    minimised by `iters` Adam steps whose gradient comes from autograd through
+    the projector (the forward's backward is the library's backprojection).
+    Returns (x, objective after each step)."""
+    from .autograd import Projector
+    A = Projector(geom, "proj", projector, "forward")
+    x = (torch.zeros(geom.vol_shape, dtype=torch.float32, device=y.device) if x0 is None
+         else x0.detach().clone().float())
+    x.requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=lr)
+    history = []
+    for _ in range(iters):
+        opt.zero_grad(set_to_none=True)
+        r = A(x) - y
+        loss = (r * r).sum()
+        if lam > 0:
+            loss = loss + lam * total_variation(x, eps)
+        loss.backward()
+        opt.step()
+        history.append(loss.detach())
+    return x.detach(), torch.stack(history).cpu().tolist()
