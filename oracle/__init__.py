@@ -74,6 +74,10 @@ def _load():
             lib.oracle_project.argtypes = [P(_Desc), C.c_int, d, d]
             lib.oracle_cell_point.argtypes = [P(_Desc), C.c_int, C.c_int, C.c_int, d]
             lib.oracle_set_threads.argtypes = [C.c_int]
+            lib.oracle_ramp_filter.argtypes = [P(_Desc), d, d, C.c_int]
+            lib.oracle_back_recon.argtypes = [P(_Desc), d, d, C.c_int]
+            lib.oracle_recon_dbeta.argtypes = [P(_Desc), C.c_int]
+            lib.oracle_recon_dbeta.restype = C.c_double
             lib.oracle_max_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -215,3 +219,39 @@ def cell_point(spec: GeometrySpec, view: int, a: int, b: int) -> np.ndarray:
     P = np.zeros(3)
     _load().oracle_cell_point(g.ref(), view, a, b, _dptr(P))
     return P
+
+
+def ramp_filter(spec: GeometrySpec, sino: np.ndarray) -> np.ndarray:
+    """Pre-weighted, ramp-filtered projections of the "recon" mode (FBP,
+    Sec. 2.3).  sino: (nview, nv, nu) or (batch, nview, nv, nu)."""
+    lib = _load()
+    g = _Geom(spec)
+    y = np.ascontiguousarray(sino, dtype=np.float64)
+    squeeze = y.ndim == 3
+    y = y.reshape((-1,) + _sino_shape(spec))
+    q = np.zeros_like(y)
+    lib.oracle_ramp_filter(g.ref(), _dptr(y), _dptr(q), y.shape[0])
+    return q[0] if squeeze else q
+
+
+def back_recon(spec: GeometrySpec, q: np.ndarray) -> np.ndarray:
+    """Recon-mode (depth-weighted, voxel-driven) backprojection of filtered
+    projections q: the second half of FBP."""
+    lib = _load()
+    g = _Geom(spec)
+    y = np.ascontiguousarray(q, dtype=np.float64)
+    squeeze = y.ndim == 3
+    y = y.reshape((-1,) + _sino_shape(spec))
+    x = np.zeros((y.shape[0],) + _vol_shape(spec))
+    lib.oracle_back_recon(g.ref(), _dptr(y), _dptr(x), y.shape[0])
+    return x[0] if squeeze else x
+
+
+def fbp(spec: GeometrySpec, sino: np.ndarray) -> np.ndarray:
+    """Filtered backprojection: back_recon(ramp_filter(sino))."""
+    return back_recon(spec, ramp_filter(spec, sino))
+
+
+def recon_dbeta(spec: GeometrySpec, view: int) -> float:
+    """The view's share of the gantry angle used by the recon mode."""
+    return float(_load().oracle_recon_dbeta(_Geom(spec).ref(), view))

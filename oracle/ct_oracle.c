@@ -660,3 +660,151 @@ void oracle_cell_point(const og_desc *g, int v, int a, int b, double *P)
     view_frame(g, v, &f);
     det_point(&f, g->curved, cell_u(g, a), cell_v(g, b), P);
 }
+
+/* ------------------------------------------------------------------ "recon" mode
+ * Filtered backprojection (Sec. 2.3: the "recon" mode backprojection carries
+ * a depth-dependent weighting, after Kak & Slaney 2001), written in the
+ * detector's own coordinates.  Per view: D = source-detector distance (flat)
+ * or detector radius (curved); (u_p, v_p) = detector coordinates measured
+ * from the principal point (the foot of the source's perpendicular), i.e.
+ * u + u0, v + h0; R = (O - s).n, the source's distance to the rotation centre
+ * O = 0 along the principal ray; dbeta = the view's share of the gantry angle.
+ *   flat:   p_w = p D / sqrt(D^2 + u_p^2 + v_p^2)
+ *           q(u_m) = du sum_n p_w(u_n) h(u_m - u_n),
+ *           h(0) = 1/(8 du^2), h(k du) = -1/(2 pi^2 k^2 du^2) for odd k, 0 for even k
+ *           f(X) = sum_views dbeta R D / ((X - s).n)^2 q(u(X), v(X))
+ *   curved: p_w = p R cos(gamma_p) D / sqrt(D^2 + v_p^2), gamma_p = u_p / D
+ *           q(u_m) = dg sum_n p_w(u_n) h_c(u_m - u_n), dg = du / D,
+ *           h_c(0) = 1/(8 dg^2), h_c(k dg) = -1/(2 pi^2 sin^2(k dg)) for odd k
+ *           f(X) = sum_views dbeta / rho^2 q(u(X), v(X)), rho^2 = ((X-s).e_u)^2 + ((X-s).n)^2
+ * with bilinear interpolation of q at the projection of the voxel centre
+ * (taps off the detector dropped).  h is half the band-limited ramp of
+ * Kak & Slaney (the backprojection runs over the full 2 pi).
+ */
+static const double OG_PI = 3.14159265358979323846;
+
+/* the view's share of the gantry angle: half the angular gap to the
+   neighbouring views on the circle (2 pi / nview when there are no angles) */
+static double recon_dbeta(const og_desc *g, int v)
+{
+    if (g->poses || g->nview == 1) return 2.0 * OG_PI / g->nview;
+    double th = fmod(g->theta[v], 2.0 * OG_PI);
+    if (th < 0) th += 2.0 * OG_PI;
+    double prev = 2.0 * OG_PI, next = 2.0 * OG_PI;
+    for (int w = 0; w < g->nview; ++w) {
+        if (w == v) continue;
+        double t = fmod(g->theta[w], 2.0 * OG_PI);
+        if (t < 0) t += 2.0 * OG_PI;
+        double fwd = fmod(t - th + 4.0 * OG_PI, 2.0 * OG_PI);  /* gap going forward */
+        double bwd = fmod(th - t + 4.0 * OG_PI, 2.0 * OG_PI);
+        if (fwd > 0 && fwd < next) next = fwd;
+        if (bwd > 0 && bwd < prev) prev = bwd;
+    }
+    return 0.5 * (prev + next);
+}
+
+static double recon_kernel(const og_desc *g, const og_frame *f, int k)
+{
+    if (k == 0) {
+        double st = g->curved ? g->du / f->D : g->du;
+        return 1.0 / (8.0 * st * st);
+    }
+    if (k % 2 == 0) return 0.0;
+    if (g->curved) {
+        double s = sin(k * g->du / f->D);
+        return -1.0 / (2.0 * OG_PI * OG_PI * s * s);
+    }
+    return -1.0 / (2.0 * OG_PI * OG_PI * (double)k * k * g->du * g->du);
+}
+
+/* q = ramp-filtered, pre-weighted projections: in, out batch x nview x nv x nu */
+int oracle_ramp_filter(const og_desc *g, const double *in, double *out, int batch)
+{
+    int nv = nv_eff(g);
+    size_t view_sz = (size_t)nv * g->nu, sstride = view_sz * g->nview;
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int v = 0; v < g->nview; ++v)
+        for (int b = 0; b < nv; ++b) {
+            og_frame f;
+            view_frame(g, v, &f);
+            double R = -dot3(f.s, f.n);
+            double vp = (g->kind == 0) ? 0.0 : cell_v(g, b) + f.h0;
+            double *pw = (double *)malloc(sizeof(double) * (size_t)g->nu);
+            double *kern = (double *)malloc(sizeof(double) * (size_t)g->nu);
+            for (int k = 0; k < g->nu; ++k) kern[k] = recon_kernel(g, &f, k);
+            double step = g->curved ? g->du / f.D : g->du;
+            for (int bt = 0; bt < batch; ++bt) {
+                const double *row = in + bt * sstride + (size_t)v * view_sz + (size_t)b * g->nu;
+                double *orow = out + bt * sstride + (size_t)v * view_sz + (size_t)b * g->nu;
+                for (int n = 0; n < g->nu; ++n) {
+                    double up = cell_u(g, n) + f.u0;
+                    double w;
+                    if (g->curved)
+                        w = R * cos(up / f.D) * f.D / sqrt(f.D * f.D + vp * vp);
+                    else
+                        w = f.D / sqrt(f.D * f.D + up * up + vp * vp);
+                    pw[n] = row[n] * w;
+                }
+                for (int m = 0; m < g->nu; ++m) {
+                    double s = 0.0;
+                    for (int n = 0; n < g->nu; ++n) s += pw[n] * kern[m > n ? m - n : n - m];
+                    orow[m] = step * s;
+                }
+            }
+            free(pw);
+            free(kern);
+        }
+    return 0;
+}
+
+/* x = recon-mode backprojection of filtered projections q (Sec. 2.3), with
+   the voxel-driven (bilinear) interpolation: vol batch x nz x ny x nx */
+int oracle_back_recon(const og_desc *g, const double *q, double *vol, int batch)
+{
+    int nz = nz_eff(g), nv = nv_eff(g);
+    size_t view_sz = (size_t)nv * g->nu, sstride = view_sz * g->nview;
+    size_t vstride = (size_t)g->nx * g->ny * nz;
+    og_frame *frames = (og_frame *)malloc(sizeof(og_frame) * (size_t)g->nview);
+    double *dbeta = (double *)malloc(sizeof(double) * (size_t)g->nview);
+    for (int v = 0; v < g->nview; ++v) {
+        view_frame(g, v, &frames[v]);
+        dbeta[v] = recon_dbeta(g, v);
+    }
+    long long total = (long long)vstride;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long vi = 0; vi < total; ++vi) {
+        int i = (int)(vi % g->nx), j = (int)((vi / g->nx) % g->ny), k = (int)(vi / ((long long)g->nx * g->ny));
+        for (int bt = 0; bt < batch; ++bt) vol[bt * vstride + vi] = 0.0;
+        for (int v = 0; v < g->nview; ++v) {
+            const og_frame *f = &frames[v];
+            double X[3], u, vv;
+            voxel_centre(g, v, i, j, k, X);
+            project(f, g->curved, X, &u, &vv);
+            double w[3] = { X[0] - f->s[0], X[1] - f->s[1], X[2] - f->s[2] };
+            double a = dot3(w, f->eu), c = dot3(w, f->n);
+            double W = g->curved ? dbeta[v] / (a * a + c * c) : dbeta[v] * (-dot3(f->s, f->n)) * f->D / (c * c);
+            double fa = u / g->du + 0.5 * (g->nu - 1);
+            double fb = (g->kind == 0) ? 0.0 : vv / g->dv + 0.5 * (nv - 1);
+            int a0 = (int)floor(fa), b0 = (int)floor(fb);
+            double ta = fa - a0, tb = fb - b0;
+            for (int db = 0; db < 2; ++db) {
+                int b = b0 + db;
+                double hb = db ? tb : 1.0 - tb;
+                if (b < 0 || b >= nv || hb == 0.0) continue;
+                for (int da = 0; da < 2; ++da) {
+                    int aa = a0 + da;
+                    double ha = da ? ta : 1.0 - ta;
+                    if (aa < 0 || aa >= g->nu || ha == 0.0) continue;
+                    for (int bt = 0; bt < batch; ++bt)
+                        vol[bt * vstride + vi] += W * ha * hb * q[bt * sstride + (size_t)v * view_sz + (size_t)b * g->nu + aa];
+                }
+            }
+        }
+    }
+    free(frames);
+    free(dbeta);
+    return 0;
+}
+
+/* the view's share of the gantry angle, as used by the recon mode */
+double oracle_recon_dbeta(const og_desc *g, int v) { return recon_dbeta(g, v); }
