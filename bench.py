@@ -287,6 +287,8 @@ def run_suite(args):
                                   "fwd_ms": tf, "back_ms": tb, "fwd_gups": upd / tf / 1e6,
                                   "back_gups": upd / tb / 1e6,
                                   "pair_gups": 2 * upd / (tf + tb) / 1e6}), flush=True)
+        if spec.kind != "noncirc3d" and (not args.suite_proj or args.suite_proj == "fbp"):
+            fbp_timing(ct, g, spec, name, args.suite_reps)
         if "curved" in name and not args.suite_proj:
             mbir_loop_timing(ct, g, spec)
         g.close()
@@ -320,6 +322,35 @@ def tv_adam_timing(ct, iters: int = 200):
                       "ms": ms, "ms_per_iteration": ms / iters, "objective_first_last": [hist[0], hist[-1]],
                       "rel_error": err}), flush=True)
     g.close()
+
+
+def fbp_timing(ct, g, spec, name: str, reps: int):
+    """Filtered backprojection (recon mode): ramp filter and depth-weighted
+    voxel-driven backprojection, timed apart, FP32."""
+    import torch
+    import workloads as W
+    x = W.phantom(spec, seed=0, device="cuda", dtype=torch.float32).reshape(g.vol_shape)
+    y = ct.forward(g, x, "sf")
+    q = torch.empty_like(y)
+    xb = torch.empty(g.vol_shape, device="cuda")
+    ct.ramp_filter(g, y, out=q)
+    ct.back_into(g, q, xb, "voxel", mode="recon")
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(reps):
+        ct.ramp_filter(g, y, out=q)
+    e[1].record()
+    for _ in range(reps):
+        ct.back_into(g, q, xb, "voxel", mode="recon")
+    e[2].record()
+    torch.cuda.synchronize()
+    tf, tb = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+    err = float((xb - x).double().norm() / x.double().norm())
+    print(json.dumps({"suite": name, "projector": "fbp (ramp filter + recon back)", "dtype": "f32",
+                      "filter_ms": tf, "back_ms": tb, "fbp_ms": tf + tb,
+                      "back_gups": spec.n_vox * spec.nview / tb / 1e6,
+                      "rel_error_vs_phantom": err}), flush=True)
 
 
 def mbir_loop_timing(ct, g, spec, steps: int = 10):

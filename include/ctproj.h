@@ -59,8 +59,19 @@ typedef enum {
     CT_SF = 3      /* separable footprint SF-TR: trapezoid x rectangle (Long et al. 2010)     */
 } ct_projector;
 
-/* Projection modes (Sec. 2.3): "proj" is the matched pair; "recon" (FBP
-   depth weighting) is not provided and returns CT_ERR_UNSUPPORTED. */
+/* Projection modes (Sec. 2.3): "proj" is the matched pair; "recon" is the
+   backprojection of filtered backprojection (FBP), which carries a
+   depth-dependent weighting instead of the projector's own weights (after
+   Kak & Slaney 2001): ct_back with CT_VOXEL backprojects ramp-filtered
+   projections (ct_ramp_filter) with bilinear interpolation and the weight
+     flat detector:   dbeta R D / ((X - s).n)^2
+     curved detector: dbeta / rho^2,  rho = distance of X from the source axis
+   where D is the source-detector distance (flat) or detector radius (curved),
+   R = (O - s).n the source's distance to the rotation centre O = 0 along the
+   detector normal, and dbeta the view's share of the gantry angle (half the
+   angular gaps to the nearest distinct view angles on either side;
+   2 pi / nview for pose-given geometries).  Other projectors, and
+   ct_forward, return CT_ERR_UNSUPPORTED in recon mode. */
 typedef enum { CT_MODE_PROJ = 0, CT_MODE_RECON = 1 } ct_mode;
 
 /* Storage types of volume and sinogram.  Arithmetic is FP32 in all cases;
@@ -201,6 +212,26 @@ ct_status ct_back_acc(const ct_geometry *geom, ct_projector proj, ct_mode mode,
  * every element it reads.  Results equal ct_back with CT_DD bit for bit. */
 ct_status ct_back_dd_noalloc(const ct_geometry *geom, ct_dtype in_t, const void *sino,
                              ct_dtype out_t, void *vol, int batch, void *cuda_stream);
+
+/* The ramp filter of filtered backprojection (the "discrete ramp filter" and
+ * "recon" mode of Sec. 2.1 and 2.3; the weights after Kak & Slaney 2001):
+ * every detector row of every view is pre-weighted and convolved with the
+ * discrete band-limited ramp, in the detector's own coordinates (u_p, v_p
+ * from the principal point, the foot of the source's perpendicular):
+ *   flat:   p D / sqrt(D^2 + u_p^2 + v_p^2), taps h(0) = 1/(8 du^2),
+ *           h(k du) = -1/(2 pi^2 k^2 du^2) for odd k, 0 for even k, times du;
+ *   curved: p R cos(u_p / D) D / sqrt(D^2 + v_p^2), taps in the angle
+ *           g = du / D: h(0) = 1/(8 g^2), h(k g) = -1/(2 pi^2 sin^2(k g)) for
+ *           odd k, times g;
+ * zero outside the row.  FBP = ct_ramp_filter, then ct_back with CT_VOXEL in
+ * CT_MODE_RECON (full scans; no short-scan weighting).
+ * sino, out: device pointers, batch x nview x nv x nu elements of in_t and
+ *   out_t; out may equal sino (same type) for an in-place filter.
+ * Errors: CT_ERR_INVALID_ARG as for ct_back; CT_ERR_UNSUPPORTED when nu >
+ *   16384 (one detector row is held in shared memory).  The paper gives the
+ *   filter's name only; the form above is Kak & Slaney's. */
+ct_status ct_ramp_filter(const ct_geometry *geom, ct_dtype in_t, const void *sino, ct_dtype out_t, void *out,
+                         int batch, void *cuda_stream);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *ct_last_error(void);

@@ -7,8 +7,8 @@ All projection work runs in hand-written sm_103a kernels behind the C ABI of
 include/ctproj.h; this package marshals PyTorch tensors to it.
 """
 from .autograd import Projector, ProjectorFn
-from .binding import (CTError, Geometry, back, back_acc, back_dd_noalloc, back_into, forward,
-                      forward_acc, forward_into, lib_path, load)
+from .binding import (CTError, Geometry, back, back_acc, back_dd_noalloc, back_into, fbp, forward,
+                      forward_acc, forward_into, lib_path, load, ramp_filter)
 
 __all__ = ["Geometry", "forward", "back", "forward_into", "back_into", "forward_acc", "back_acc",
-           "back_dd_noalloc", "ProjectorFn", "Projector", "CTError", "load", "lib_path"]
+           "back_dd_noalloc", "ramp_filter", "fbp", "ProjectorFn", "Projector", "CTError", "load", "lib_path"]

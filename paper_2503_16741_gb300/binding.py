@@ -91,6 +91,8 @@ def load():
         lib.ct_back_dd_noalloc.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                            C.c_int, C.c_void_p]
         lib.ct_back_dd_noalloc.restype = C.c_int
+        lib.ct_ramp_filter.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
+        lib.ct_ramp_filter.restype = C.c_int
         lib.ct_last_error.restype = C.c_char_p
         lib.ct_version.restype = C.c_char_p
         for f in ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_shape", "ct_forward", "ct_back"):
@@ -289,6 +291,27 @@ def back(geom: Geometry, y: torch.Tensor, projector: str = "sf", mode: str = "pr
     lead = y.shape[:-len(geom.sino_shape)]
     x = torch.empty(tuple(lead) + geom.vol_shape, dtype=out_dtype or y.dtype, device=y.device)
     return back_into(geom, y, x, projector, mode, stream)
+
+
+def ramp_filter(geom: Geometry, y: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """The pre-weighted discrete ramp filter of FBP (ct_ramp_filter), row by
+    row; `out` may be `y` itself for an in-place filter."""
+    _check_tensor(y, "sinogram")
+    batch = _batch_of(y, geom.sino_shape, "sinogram")
+    if out is None:
+        out = torch.empty_like(y)
+    _check_tensor(out, "output")
+    if out.shape != y.shape:
+        raise ValueError("output shape differs from the sinogram's")
+    _check(load().ct_ramp_filter(geom.handle, DTYPES[y.dtype], y.data_ptr(), DTYPES[out.dtype], out.data_ptr(),
+                                 batch, _stream_ptr(stream)))
+    return out
+
+
+def fbp(geom: Geometry, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """Filtered backprojection: the ramp filter, then the recon-mode
+    (depth-weighted, voxel-driven) backprojection (Sec. 2.3)."""
+    return back(geom, ramp_filter(geom, y, stream=stream), "voxel", mode="recon", stream=stream)
 
 
 def back_dd_noalloc(geom: Geometry, y: torch.Tensor, out_dtype: Optional[torch.dtype] = None,

@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libctproj.so")
-SOURCES = ["ct_capi.cpp", "ct_workspace.cpp", "ct_noalloc.cu", "k_sf.cu", "k_nc_fwd.cu", "k_nc_back.cu", "k_dd.cu", "k_voxel.cu", "k_ray.cu"]
+SOURCES = ["ct_capi.cpp", "ct_workspace.cpp", "ct_noalloc.cu", "k_sf.cu", "k_nc_fwd.cu", "k_nc_back.cu", "k_dd.cu", "k_voxel.cu", "k_ray.cu", "k_fbp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-O2", "-I" + os.path.join(ROOT, "include")]

@@ -100,6 +100,31 @@ void view_pose(const ct_geometry_desc *d, int v, const Param P[], Vec3 &s, Vec3 
     ev = R * Vec3{0, 0, 1};
 }
 
+// Recon mode (FBP): each view's share of the gantry angle, half the angular
+// gaps to the nearest distinct view angles on either side (2 pi / nview for
+// an equally spaced full scan; 2 pi / nview for pose-given geometries).
+std::vector<double> recon_dbetas(const ct_geometry_desc *d, const Param P[]) {
+    const double two_pi = 2.0 * M_PI;
+    std::vector<double> out(d->nview, two_pi / d->nview);
+    if (d->poses || d->nview == 1) return out;
+    std::vector<double> th(d->nview);
+    for (int v = 0; v < d->nview; ++v) {
+        double t = std::fmod(P[0].at(v), two_pi);
+        th[v] = t < 0 ? t + two_pi : t;
+    }
+    std::vector<double> u(th);
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
+    const size_t m = u.size();
+    for (int v = 0; v < d->nview; ++v) {
+        const size_t i = std::lower_bound(u.begin(), u.end(), th[v]) - u.begin();
+        const double next = m == 1 ? two_pi : (i + 1 < m ? u[i + 1] - u[i] : u[0] + two_pi - u[i]);
+        const double prev = m == 1 ? two_pi : (i > 0 ? u[i] - u[i - 1] : u[i] + two_pi - u[m - 1]);
+        out[v] = 0.5 * (prev + next);
+    }
+    return out;
+}
+
 }  // namespace
 
 void ctp::set_last_error(const std::string &msg) { g_err = msg; }
@@ -154,6 +179,7 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
     g->dv = two_d ? 1.0 : d->dv;
     const bool curved = d->det == CT_DET_CURVED;
     g->host_views.resize(d->nview);
+    const std::vector<double> dbeta = recon_dbetas(d, P);
 
     for (int v = 0; v < d->nview; ++v) {
         Vec3 s, c, eu, ev;
@@ -193,6 +219,19 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
         V.Cv = (float)(0.5 * (g->nv - 1) - h0 / g->dv);
         V.D = (float)D;
         V.main_y = std::fabs(cs.y) >= std::fabs(cs.x) ? 1 : 0;
+        const double R = -dot(s, n);  // recon mode: source to rotation centre along n
+        V.rc_R = (float)R;
+        const double db = dbeta[v];
+        V.rc_w = (float)(curved ? db : db * R * D);
+        {  // ramp's response to a constant row, in FP64 (a small difference of large sums)
+            const double st = curved ? g->du / D : g->du;
+            double sum = 1.0 / (8.0 * st * st);
+            for (int k = 1; k < g->nu; k += 2) {
+                const double den = curved ? std::sin(k * st) : k * st;
+                sum -= 1.0 / (M_PI * M_PI * den * den);
+            }
+            V.rc_c = (float)(st * sum);
+        }
 
         // The volume must lie between source and detector; bound the
         // footprint extents (in cells) for the forward-gather search windows.
@@ -317,8 +356,9 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
                          void *stream) {
     if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");
     if (proj < CT_VOXEL || proj > CT_SF) return fail(CT_ERR_INVALID_ARG, "unknown projector");
-    if (mode == CT_MODE_RECON) return fail(CT_ERR_UNSUPPORTED, "recon mode (FBP depth weighting) is not provided");
-    if (mode != CT_MODE_PROJ) return fail(CT_ERR_INVALID_ARG, "unknown mode");
+    if (mode != CT_MODE_PROJ && mode != CT_MODE_RECON) return fail(CT_ERR_INVALID_ARG, "unknown mode");
+    if (mode == CT_MODE_RECON && (dir != 1 || proj != CT_VOXEL))
+        return fail(CT_ERR_UNSUPPORTED, "recon mode is the voxel-driven FBP backprojection (ct_back, CT_VOXEL)");
     if (in_t < CT_F32 || in_t > CT_BF16 || out_t < CT_F32 || out_t > CT_BF16)
         return fail(CT_ERR_INVALID_ARG, "unknown dtype");
     if (!in || !out) return fail(CT_ERR_INVALID_ARG, "null data pointer");
@@ -342,7 +382,9 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     G.alpha = alpha;
     G.beta = beta;
     cudaError_t e;
-    switch (proj) {
+    if (mode == CT_MODE_RECON) proj = CT_VOXEL;
+    switch (mode == CT_MODE_RECON ? -1 : (int)proj) {
+    case -1: e = ctp::launch_voxel_recon(G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_VOXEL: e = ctp::launch_voxel(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_RAY: e = ctp::launch_ray(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_DD: e = ctp::launch_dd(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
@@ -371,6 +413,29 @@ ct_status ct_forward_acc(const ct_geometry *g, ct_projector proj, ct_mode mode, 
 ct_status ct_back_acc(const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t, const void *sino,
                       ct_dtype out_t, void *vol, int batch, float alpha, float beta, void *cuda_stream) {
     return project(1, g, proj, mode, in_t, sino, out_t, vol, batch, alpha, beta, cuda_stream);
+}
+
+ct_status ct_ramp_filter(const ct_geometry *g, ct_dtype in_t, const void *sino, ct_dtype out_t, void *out, int batch,
+                         void *cuda_stream) {
+    if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");
+    if (in_t < CT_F32 || in_t > CT_BF16 || out_t < CT_F32 || out_t > CT_BF16)
+        return fail(CT_ERR_INVALID_ARG, "unknown dtype");
+    if (!sino || !out) return fail(CT_ERR_INVALID_ARG, "null data pointer");
+    if (batch < 1) return fail(CT_ERR_INVALID_ARG, "batch must be >= 1");
+    if (sino == out && in_t != out_t) return fail(CT_ERR_INVALID_ARG, "an in-place filter keeps the type");
+    if (g->nu > 16384) return fail(CT_ERR_UNSUPPORTED, "rows longer than 16384 cells");
+    if ((long long)g->nv * g->nview * batch > 2147483647LL) return fail(CT_ERR_INVALID_ARG, "too many rows");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
+        return fail(CT_ERR_INVALID_ARG, "the geometry's device is not the current device");
+    ct_status st = check_ptr(sino, "input");
+    if (st != CT_OK) return st;
+    st = check_ptr(out, "output");
+    if (st != CT_OK) return st;
+    cudaError_t e = ctp::launch_ramp_filter(g->grid, g->dev_views, in_t, sino, out_t, out, batch,
+                                            static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return CT_OK;
 }
 
 }  // extern "C"

@@ -23,6 +23,12 @@ cudaError_t launch_nc(int dd, int dir, const CtGrid &g, const CtView *views, int
 // voxel-driven forward in circular geometry (the streaming forward of k_sf.cu)
 cudaError_t launch_vx_fwd_circ(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                                void *out, int batch, cudaStream_t st);
+// recon mode (FBP): the pre-weighted ramp filter of each detector row, and the
+// depth-weighted voxel-driven backprojection of the filtered projections
+cudaError_t launch_ramp_filter(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                               void *out, int batch, cudaStream_t st);
+cudaError_t launch_voxel_recon(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                               void *out, int batch, cudaStream_t st);
 cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                          int out_t, void *out, int batch, cudaStream_t st);
 cudaError_t launch_ray(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,

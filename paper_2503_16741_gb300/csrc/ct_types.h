@@ -30,7 +30,9 @@ struct alignas(16) CtView {
     float m_sf_u;     // bound on |fu(corner) - fu(centre)| over the volume (SF), cells
     float m_sf_v;     // bound on |fv(z +- dz/2) - fv(centre)| (SF and DD), rows
     float m_dd_u;     // bound on |fu(boundary point) - fu(centre)| (DD), cells
-    float pad[3];
+    float rc_w;       // recon mode: flat dbeta R D, curved dbeta (dbeta = the view's share of the gantry angle)
+    float rc_R;       // recon mode: R = (O - s).n, the source's distance to the rotation centre O
+    float rc_c;       // recon mode: step (h0 + 2 sum_{odd k < nu} h_k), the ramp's response to a constant row
 };
 static_assert(sizeof(CtView) == 40 * 4, "CtView layout");
 

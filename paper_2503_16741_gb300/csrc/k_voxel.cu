@@ -16,6 +16,7 @@ namespace ctp {
 // non-circular: per voxel
 struct VxVox {
     float fu, fv, amp;
+    float den;  // depth (X - s).n
 };
 __device__ __forceinline__ VxVox vx_vox_nc(const CtView &V, const CtGrid &g, int i, int j, int k) {
     const float fi = (float)i, fj = (float)j, fk = (float)k;
@@ -28,6 +29,7 @@ __device__ __forceinline__ VxVox vx_vox_nc(const CtView &V, const CtGrid &g, int
     const float wx = fmaf(fi, g.dx, V.o[0]), wy = fmaf(fj, g.dy, V.o[1]);
     const float wz = fmaf(fk, g.dz, V.o[2]);
     P.amp = vx_amp(g, V, sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz))), cn);
+    P.den = cn;
     return P;
 }
 
@@ -60,7 +62,11 @@ __device__ __forceinline__ float bilinear(const TIn *yv, const CtGrid &g, float 
     return s;
 }
 
-template <typename TIn, bool CURVED, int ZT>
+// RECON: the recon-mode (FBP) backprojection of filtered projections (Sec.
+// 2.3): the same bilinear interpolation with the depth weight in place of the
+// voxel-driven amplitude, rc_w / depth^2 (flat: dbeta R D / ((X-s).n)^2;
+// curved: dbeta / rho^2), constant down a column in circular geometry.
+template <typename TIn, bool CURVED, int ZT, bool RECON = false>
 __global__ void __launch_bounds__(128)
 vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
@@ -82,12 +88,13 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
         const VxCol C = vx_col<CURVED>(V, g, i, j);
         if (C.fu <= -1.f || C.fu >= (float)g.nu) continue;
         const TIn *yv = ys + (size_t)v * vstride;
+        const float wr = RECON ? V.rc_w / (C.den * C.den) : 0.f;
 #pragma unroll
         for (int kk = 0; kk < ZT; ++kk) {
             const int k = kbeg + kk;
             if (k >= g.nz) break;
             const float fv = fmaf(C.sv, (float)k, C.fv0);
-            acc[kk] = fmaf(vx_amp_col(C, g, V, k), bilinear(yv, g, C.fu, fv), acc[kk]);
+            acc[kk] = fmaf(RECON ? wr : vx_amp_col(C, g, V, k), bilinear(yv, g, C.fu, fv), acc[kk]);
         }
     }
     const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
@@ -98,7 +105,7 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
     }
 }
 
-template <typename TIn, int ZT>
+template <typename TIn, int ZT, bool RECON = false>
 __global__ void __launch_bounds__(128)
 vx_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
            void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
@@ -123,7 +130,7 @@ vx_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
             const int k = kbeg + kk;
             if (k >= g.nz) break;
             const VxVox P = vx_vox_nc(V, g, i, j, k);
-            acc[kk] = fmaf(P.amp, bilinear(yv, g, P.fu, P.fv), acc[kk]);
+            acc[kk] = fmaf(RECON ? V.rc_w / (P.den * P.den) : P.amp, bilinear(yv, g, P.fu, P.fv), acc[kk]);
         }
     }
     const size_t base = (size_t)bt * g.nz * g.ny * g.nx + (size_t)j * g.nx + i;
@@ -197,6 +204,32 @@ cudaError_t vx_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
     return cudaGetLastError();
 }
 }  // namespace
+
+namespace {
+template <typename TIn>
+cudaError_t vx_recon_t(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
+                       cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+    dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+    if (g.variant == GEO_NONCIRC_FLAT)
+        vx_back_nc<TIn, kZT, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    else if (g.variant == GEO_CIRC_CURVED)
+        vx_back_circ<TIn, true, kZT, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    else
+        vx_back_circ<TIn, false, kZT, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_voxel_recon(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                               void *out, int batch, cudaStream_t st) {
+    switch (in_t) {
+    case 0: return vx_recon_t<float>(g, views, in, out, out_t, batch, st);
+    case 1: return vx_recon_t<__half>(g, views, in, out, out_t, batch, st);
+    default: return vx_recon_t<__nv_bfloat16>(g, views, in, out, out_t, batch, st);
+    }
+}
 
 cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                          int out_t, void *out, int batch, cudaStream_t st) {
