@@ -31,7 +31,7 @@ _LIB = os.path.join(_HERE, "libctoracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PROJECTORS = {"voxel": 0, "ray": 1, "dd": 2, "sf": 3}
+PROJECTORS = {"voxel": 0, "ray": 1, "dd": 2, "sf": 3, "sftt": 4}
 KINDS = {"fan2d": 0, "circ3d": 1, "noncirc3d": 2}
 
 

@@ -26,7 +26,9 @@
  *
  * Projectors (Sec. 2.3): 0 voxel-driven (point voxel, bilinear detector
  * interpolation), 1 ray-driven (Siddon line lengths), 2 distance-driven
- * (boundary overlaps), 3 separable footprint SF-TR (trapezoid x rectangle).
+ * (boundary overlaps), 3 separable footprint SF-TR (trapezoid x rectangle),
+ * 4 SF-TT (trapezoid x trapezoid, per-cell amplitude; the cited method's
+ * variant for large cone angles).
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,7 +59,7 @@ typedef struct {
     double h0;  /* (c - s).e_v */
 } og_frame;
 
-enum { OG_VOXEL = 0, OG_RAY = 1, OG_DD = 2, OG_SF = 3 };
+enum { OG_VOXEL = 0, OG_RAY = 1, OG_DD = 2, OG_SF = 3, OG_SFTT = 4 };
 #define OG_FP_CAP 8192
 
 typedef struct {
@@ -333,6 +335,63 @@ static void fp_sf(const og_desc *g, const og_frame *f, int v, int i, int j, int 
     }
 }
 
+/* ---------- separable footprint SF-TT (Long, Fessler & Balter 2010):
+   the transaxial trapezoid of SF-TR times an axial trapezoid, with the
+   amplitude of each detector cell ("A2": the SF-TR amplitude taken along the
+   ray to the cell centre instead of the ray to the voxel centre).  The axial
+   trapezoid's knots are the projections of the voxel's two z faces (z -+ dz/2)
+   at its transaxial corners nearest to and farthest from the source (least
+   and greatest depth (P - s).n), sorted. */
+static void fp_sftt(const og_desc *g, const og_frame *f, int v, int i, int j, int k, og_fp *fp)
+{
+    double X[3], P[3], tau[4], tv[4], depth[4], tmp;
+    voxel_centre(g, v, i, j, k, X);
+    double dz = eff_dz(g), dv = eff_dv(g);
+    int q = 0, qn = 0, qf = 0;
+    for (int sx = -1; sx <= 1; sx += 2)
+        for (int sy = -1; sy <= 1; sy += 2) {
+            P[0] = X[0] + 0.5 * sx * g->dx;
+            P[1] = X[1] + 0.5 * sy * g->dy;
+            P[2] = X[2];
+            project(f, g->curved, P, &tau[q], &tmp);
+            double w[3] = { P[0] - f->s[0], P[1] - f->s[1], P[2] - f->s[2] };
+            depth[q] = dot3(w, f->n);
+            if (depth[q] < depth[qn]) qn = q;
+            if (depth[q] > depth[qf]) qf = q;
+            ++q;
+        }
+    sort4(tau);
+    q = 0;
+    for (int c = 0; c < 2; ++c) {
+        int sx = ((c ? qf : qn) & 2) ? 1 : -1, sy = ((c ? qf : qn) & 1) ? 1 : -1;
+        for (int sz = -1; sz <= 1; sz += 2) {
+            P[0] = X[0] + 0.5 * sx * g->dx;
+            P[1] = X[1] + 0.5 * sy * g->dy;
+            P[2] = X[2] + 0.5 * sz * dz;
+            project(f, g->curved, P, &tmp, &tv[q++]);
+        }
+    }
+    sort4(tv);
+    int a0, a1, b0, b1;
+    cell_range(tau[0], tau[3], g->du, g->nu, &a0, &a1);
+    cell_range(tv[0], tv[3], dv, g->nv, &b0, &b1);
+    for (int b = b0; b <= b1; ++b) {
+        double vc = cell_v(g, b);
+        double Fv = (trap_integral(tv, vc + 0.5 * dv) - trap_integral(tv, vc - 0.5 * dv)) / dv;
+        if (Fv == 0.0) continue;
+        for (int a = a0; a <= a1; ++a) {
+            double uc = cell_u(g, a);
+            double Fu = (trap_integral(tau, uc + 0.5 * g->du) - trap_integral(tau, uc - 0.5 * g->du)) / g->du;
+            if (Fu == 0.0) continue;
+            double C[3];
+            det_point(f, g->curved, uc, vc, C);
+            double d[3] = { C[0] - f->s[0], C[1] - f->s[1], C[2] - f->s[2] };
+            double amp = g->dx * norm3(d) / dmax(fabs(d[0]), fabs(d[1]));
+            fp_push(fp, a, b, amp * Fu * Fv);
+        }
+    }
+}
+
 /* ---------- ray-driven (Siddon 1985) */
 /* length of the segment s -> P inside the half-open box [lo, hi) */
 static double seg_in_box(const double *s, const double *P, const double *lo, const double *hi)
@@ -413,6 +472,7 @@ static void footprint(const og_desc *g, const og_frame *f, int proj, int v, int 
     case OG_VOXEL: fp_voxel(g, f, v, i, j, k, fp); break;
     case OG_RAY:   fp_ray(g, f, v, i, j, k, fp); break;
     case OG_DD:    fp_dd(g, f, v, i, j, k, fp); break;
+    case OG_SFTT:  fp_sftt(g, f, v, i, j, k, fp); break;
     default:       fp_sf(g, f, v, i, j, k, fp); break;
     }
 }
