@@ -246,9 +246,9 @@ def run_suite(args):
     torch.cuda.set_device(0)
     dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
     cases = [("fan2d 128^2, 180 views, 256 bins", W.fan2d_small(), ["ray", "voxel", "dd", "sf"], ["f32"]),
-             ("circ 256^3, 360 views, 512x384", W.circ3d_256(), ["sf", "dd", "voxel", "ray"], ["f32", "f16"]),
+             ("circ 256^3, 360 views, 512x384", W.circ3d_256(), ["sf", "dd", "voxel", "ray", "sftt"], ["f32", "f16"]),
              ("circ curved 512^2x128, 984 views, 888x64", W.circ3d_curved(), ["dd", "sf"], ["f32"]),
-             ("saddle 512^3, 500 views, 1024^2", W.noncirc3d_saddle(), ["sf", "dd"], ["f32", "f16", "bf16"])]
+             ("saddle 512^3, 500 views, 1024^2", W.noncirc3d_saddle(), ["sf", "dd", "sftt"], ["f32", "f16", "bf16"])]
     if not args.suite_filter or args.suite_filter in "sinusoidal":
         tv_adam_timing(ct)
     for name, spec, projs, dtypes in cases:

@@ -56,7 +56,10 @@ typedef enum {
     CT_VOXEL = 0,  /* voxel-driven: point voxel, bilinear detector interpolation (Peters 1981) */
     CT_RAY = 1,    /* ray-driven: exact chord lengths of the cell-centre ray (Siddon 1985)     */
     CT_DD = 2,     /* distance-driven: boundary overlaps (De Man & Basu 2004)                 */
-    CT_SF = 3      /* separable footprint SF-TR: trapezoid x rectangle (Long et al. 2010)     */
+    CT_SF = 3,     /* separable footprint SF-TR: trapezoid x rectangle (Long et al. 2010)     */
+    CT_SF_TT = 4   /* SF-TT: trapezoid x trapezoid, amplitude per detector cell ("A2"; the
+                      same paper's variant for large cone angles); flat detectors, square
+                      voxels, footprints of at most 8 cells x 4 rows (else UNSUPPORTED)   */
 } ct_projector;
 
 /* Projection modes (Sec. 2.3): "proj" is the matched pair; "recon" is the

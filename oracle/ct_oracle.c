@@ -341,29 +341,31 @@ static void fp_sf(const og_desc *g, const og_frame *f, int v, int i, int j, int 
    ray to the cell centre instead of the ray to the voxel centre).  The axial
    trapezoid's knots are the projections of the voxel's two z faces (z -+ dz/2)
    at its transaxial corners nearest to and farthest from the source (least
-   and greatest depth (P - s).n), sorted. */
+   and greatest depth (P - s).n), sorted.  The nearest corner is the one
+   against the detector normal's transaxial components (x offset -sign(n_x) dx/2,
+   likewise y); a component below 1e-7 counts as zero and takes the negative
+   side for both corners (the two candidates then lie at the same depth). */
 static void fp_sftt(const og_desc *g, const og_frame *f, int v, int i, int j, int k, og_fp *fp)
 {
     double X[3], P[3], tau[4], tv[4], depth[4], tmp;
     voxel_centre(g, v, i, j, k, X);
     double dz = eff_dz(g), dv = eff_dv(g);
-    int q = 0, qn = 0, qf = 0;
+    int q = 0;
     for (int sx = -1; sx <= 1; sx += 2)
         for (int sy = -1; sy <= 1; sy += 2) {
             P[0] = X[0] + 0.5 * sx * g->dx;
             P[1] = X[1] + 0.5 * sy * g->dy;
             P[2] = X[2];
-            project(f, g->curved, P, &tau[q], &tmp);
-            double w[3] = { P[0] - f->s[0], P[1] - f->s[1], P[2] - f->s[2] };
-            depth[q] = dot3(w, f->n);
-            if (depth[q] < depth[qn]) qn = q;
-            if (depth[q] > depth[qf]) qf = q;
-            ++q;
+            project(f, g->curved, P, &tau[q++], &tmp);
         }
     sort4(tau);
+    const double eps = 1e-7;
+    const int nx_sx = f->n[0] < -eps ? 1 : -1, ny_sy = f->n[1] < -eps ? 1 : -1;  /* nearest */
+    const int fx_sx = f->n[0] > eps ? 1 : -1, fy_sy = f->n[1] > eps ? 1 : -1;    /* farthest */
+    (void)depth;
     q = 0;
     for (int c = 0; c < 2; ++c) {
-        int sx = ((c ? qf : qn) & 2) ? 1 : -1, sy = ((c ? qf : qn) & 1) ? 1 : -1;
+        int sx = c ? fx_sx : nx_sx, sy = c ? fy_sy : ny_sy;
         for (int sz = -1; sz <= 1; sz += 2) {
             P[0] = X[0] + 0.5 * sx * g->dx;
             P[1] = X[1] + 0.5 * sy * g->dy;

@@ -22,7 +22,7 @@ STATUS = {0: "CT_OK", 1: "CT_ERR_INVALID_ARG", 2: "CT_ERR_UNSUPPORTED", 3: "CT_E
           4: "CT_ERR_OOM", 5: "CT_ERR_TIMEOUT"}
 KINDS = {"fan2d": 0, "circ3d": 1, "noncirc3d": 2}
 DETS = {"flat": 0, "curved": 1}
-PROJECTORS = {"voxel": 0, "ray": 1, "dd": 2, "sf": 3}
+PROJECTORS = {"voxel": 0, "ray": 1, "dd": 2, "sf": 3, "sftt": 4}
 MODES = {"proj": 0, "recon": 1}
 DTYPES = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}
 PER_VIEW = ("theta", "phi", "psi", "sad", "sdd", "x_src", "z_src",

@@ -264,6 +264,11 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
         V.m_sf_u = (float)bound(D / g->du, hx * std::fabs(eu.x) + hy * std::fabs(eu.y),
                                 hx * std::fabs(n.x) + hy * std::fabs(n.y), tu);
         V.m_sf_v = (float)bound(D / g->dv, hz * std::fabs(ev.z), hz * std::fabs(n.z), tv);
+        // SF-TT: the z faces at the transaxial corners (a 2D row lies inside the
+        // axial plateau, so its factor is 1 and the bound does not matter)
+        V.m_tt_v = two_d ? 0.25f
+                         : (float)bound(D / g->dv, hx * std::fabs(ev.x) + hy * std::fabs(ev.y) + hz * std::fabs(ev.z),
+                                        hx * std::fabs(n.x) + hy * std::fabs(n.y) + hz * std::fabs(n.z), tv);
         if (V.main_y)
             V.m_dd_u = (float)bound(D / g->du, hx * std::fabs(eu.x), hx * std::fabs(n.x), tu);
         else
@@ -287,10 +292,12 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
     G.max_m_sf_u = 0.f;
     G.max_m_dd_u = 0.f;
     G.max_m_sf_v = 0.f;
+    G.max_m_tt_v = 0.f;
     for (const CtView &V : g->host_views) {
         G.max_m_sf_u = std::max(G.max_m_sf_u, V.m_sf_u);
         G.max_m_dd_u = std::max(G.max_m_dd_u, V.m_dd_u);
         G.max_m_sf_v = std::max(G.max_m_sf_v, V.m_sf_v);
+        G.max_m_tt_v = std::max(G.max_m_tt_v, V.m_tt_v);
     }
 
     if (cudaGetDevice(&g->device) != cudaSuccess) {
@@ -355,7 +362,7 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
                          const void *in, ct_dtype out_t, void *out, int batch, float alpha, float beta,
                          void *stream) {
     if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");
-    if (proj < CT_VOXEL || proj > CT_SF) return fail(CT_ERR_INVALID_ARG, "unknown projector");
+    if (proj < CT_VOXEL || proj > CT_SF_TT) return fail(CT_ERR_INVALID_ARG, "unknown projector");
     if (mode != CT_MODE_PROJ && mode != CT_MODE_RECON) return fail(CT_ERR_INVALID_ARG, "unknown mode");
     if (mode == CT_MODE_RECON && (dir != 1 || proj != CT_VOXEL))
         return fail(CT_ERR_UNSUPPORTED, "recon mode is the voxel-driven FBP backprojection (ct_back, CT_VOXEL)");
@@ -363,8 +370,12 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
         return fail(CT_ERR_INVALID_ARG, "unknown dtype");
     if (!in || !out) return fail(CT_ERR_INVALID_ARG, "null data pointer");
     if (batch < 1) return fail(CT_ERR_INVALID_ARG, "batch must be >= 1");
-    if (proj == CT_SF && std::fabs(g->dx - g->dy) > 1e-9 * g->dx)
+    if ((proj == CT_SF || proj == CT_SF_TT) && std::fabs(g->dx - g->dy) > 1e-9 * g->dx)
         return fail(CT_ERR_UNSUPPORTED, "the SF amplitude needs square voxels (dx == dy)");
+    if (proj == CT_SF_TT && g->grid.variant == ctp::GEO_CIRC_CURVED)
+        return fail(CT_ERR_UNSUPPORTED, "SF-TT is provided for flat detectors");
+    if (proj == CT_SF_TT && !ctp::nc_footprint_fits(g->grid, 2))
+        return fail(CT_ERR_UNSUPPORTED, "SF-TT footprints wider than 8 cells or taller than 4 rows");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
         return fail(CT_ERR_INVALID_ARG, "the geometry's device is not the current device");
@@ -388,6 +399,7 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     case CT_VOXEL: e = ctp::launch_voxel(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_RAY: e = ctp::launch_ray(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_DD: e = ctp::launch_dd(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    case CT_SF_TT: e = ctp::launch_sftt(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     default: e = ctp::launch_sf(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     }
     if (e == cudaErrorMemoryAllocation) return fail(CT_ERR_OOM, "workspace allocation failed");

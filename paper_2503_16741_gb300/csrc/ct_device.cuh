@@ -202,6 +202,17 @@ __device__ __forceinline__ float dd_len(const CtView &V, const CtGrid &g, int a,
     return (m ? g.dy : g.dx) * sqrtf(d2) / fabsf(dm);
 }
 
+// SF-TT amplitude ("A2") of cell (a, b) on a flat detector: the SF-TR
+// amplitude taken along the ray to the cell centre, dx |d| / max(|d_x|, |d_y|)
+// with d = (cell centre - source) in world coordinates.
+__device__ __forceinline__ float tt_amp(const CtView &V, const CtGrid &g, int a, int b) {
+    const float U = g.du * ((float)a - V.Cu), Vb = g.dv * ((float)b - V.Cv);
+    const float dx_ = fmaf(V.D, V.nn[0], fmaf(U, V.eu[0], Vb * V.ev[0]));
+    const float dy_ = fmaf(V.D, V.nn[1], fmaf(U, V.eu[1], Vb * V.ev[1]));
+    const float dz_ = fmaf(V.D, V.nn[2], fmaf(U, V.eu[2], Vb * V.ev[2]));
+    return g.dx * sqrtf(fmaf(dx_, dx_, fmaf(dy_, dy_, dz_ * dz_))) / fmaxf(fabsf(dx_), fabsf(dy_));
+}
+
 // ---------------------------------------------------------------- forward search
 // Candidate lateral/axial index box of slab s for the detector window
 // fu in [Flo, Fhi], fv in [Glo, Ghi] of a flat detector: the window's four

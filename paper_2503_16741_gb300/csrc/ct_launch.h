@@ -14,11 +14,14 @@ cudaError_t launch_dd(int dir, const CtGrid &g, const CtView *views, int in_t, c
                       int out_t, void *out, int batch, cudaStream_t st);
 cudaError_t launch_dd_nc(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                          int out_t, void *out, int batch, cudaStream_t st);
-// SF (dd = 0) or DD (dd = 1) in non-circular geometry for footprints of at
-// most 8 cells by 4 rows (nc_footprint_fits); the DD back direction takes
-// the sinogram already scaled by each cell's path length.
-bool nc_footprint_fits(const CtGrid &g, int dd);
-cudaError_t launch_nc(int dd, int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+// SF-TR (kind 0), DD (1) or SF-TT (2) with per-voxel footprints (any flat
+// detector) of at most 8 cells by 4 rows (nc_footprint_fits); the DD and
+// SF-TT back directions take the sinogram already scaled by each cell's
+// factor (launch_sftt does that for SF-TT).
+bool nc_footprint_fits(const CtGrid &g, int kind);
+cudaError_t launch_sftt(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                        void *out, int batch, cudaStream_t st);
+cudaError_t launch_nc(int kind, int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st);
 // voxel-driven forward in circular geometry (the streaming forward of k_sf.cu)
 cudaError_t launch_vx_fwd_circ(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,

@@ -33,8 +33,10 @@ struct alignas(16) CtView {
     float rc_w;       // recon mode: flat dbeta R D, curved dbeta (dbeta = the view's share of the gantry angle)
     float rc_R;       // recon mode: R = (O - s).n, the source's distance to the rotation centre O
     float rc_c;       // recon mode: step (h0 + 2 sum_{odd k < nu} h_k), the ramp's response to a constant row
+    float m_tt_v;     // bound on the SF-TT axial knots' distance from fv(centre), rows
+    float pad[3];
 };
-static_assert(sizeof(CtView) == 40 * 4, "CtView layout");
+static_assert(sizeof(CtView) == 44 * 4, "CtView layout");
 
 enum GeoVariant { GEO_CIRC_FLAT = 0, GEO_CIRC_CURVED = 1, GEO_NONCIRC_FLAT = 2 };
 
@@ -49,6 +51,7 @@ struct CtGrid {
     float max_m_sf_u;  // largest per-view SF transaxial footprint bound (cells)
     float max_m_dd_u;  // largest per-view DD boundary bound (cells)
     float max_m_sf_v;  // largest per-view axial half-height bound (rows)
+    float max_m_tt_v;  // largest per-view SF-TT axial bound (rows)
     float alpha, beta; // output epilogue: out = alpha * result + beta * out
 };
 

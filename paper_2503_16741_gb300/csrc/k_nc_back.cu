@@ -1,6 +1,6 @@
 // k_nc_back.cu -- backprojection of the non-circular SF-TR and DD footprint
-// projectors, and the entry for both directions (the footprint and the
-// dispatch are in k_nc.cuh).
+// projectors and of SF-TT, and the entries for both directions (the
+// footprint and the dispatch are in k_nc.cuh).
 #include "k_nc.cuh"
 
 namespace ctp {
@@ -14,7 +14,7 @@ constexpr int kNcViews = 16;
 // runs over its voxels one at a time (the per-voxel body appears once in the
 // code, which keeps the kernel within the instruction cache) with the
 // voxel's sum carried in shared memory between rounds.
-template <typename TIn, bool DD, int NA, int NB, int ZT>
+template <typename TIn, int KIND, int NA, int NB, int ZT>
 __global__ void __launch_bounds__(128, 8)
 nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino, void *__restrict__ vol,
         int out_t, int tiles_x, int nzc) {
@@ -53,7 +53,7 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
                 const CtView &V = sview[vv];
                 const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
                 NcFp<NA, NB> P;
-                nc_fp<DD, NA, NB>(V, g, i, j, k, P);
+                nc_fp<KIND, NA, NB>(V, g, i, j, k, P);
                 // cells off the detector get weight 0 and a clamped (in-bounds)
                 // address; cells past the footprint are not read
                 int ac[NA];
@@ -95,33 +95,73 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
 }
 
 namespace {
-template <typename TIn, bool DD, int NA, int NB> struct NcBack {
+template <typename TIn, int KIND, int NA, int NB> struct NcBack {
     static cudaError_t go(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
                           cudaStream_t st) {
         constexpr int ZT = 8;
         const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + ZT - 1) / ZT;
         dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-        nc_back<TIn, DD, NA, NB, ZT><<<grd, blk, 0, st>>>(g, views, static_cast<const TIn *>(in), out, out_t,
+        nc_back<TIn, KIND, NA, NB, ZT><<<grd, blk, 0, st>>>(g, views, static_cast<const TIn *>(in), out, out_t,
                                                           tiles_x, nzc);
         return cudaGetLastError();
     }
 };
 }  // namespace
 
-cudaError_t launch_nc_back(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+cudaError_t launch_nc_back(int kind, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                            void *out, int batch, cudaStream_t st) {
-    return nc_dispatch<NcBack>(dd, in_t, g, views, in, out, out_t, batch, st);
+    return nc_dispatch<NcBack>(kind, in_t, g, views, in, out, out_t, batch, st);
 }
 
-bool nc_footprint_fits(const CtGrid &g, int dd) {
+bool nc_footprint_fits(const CtGrid &g, int kind) {
     // at most 8 cells (half width <= 3.5) by 4 rows (half height <= 1.5)
-    return (dd ? g.max_m_dd_u : g.max_m_sf_u) <= 3.5f && g.max_m_sf_v <= 1.5f;
+    return (kind == NC_DD ? g.max_m_dd_u : g.max_m_sf_u) <= 3.5f &&
+           (kind == NC_TT ? g.max_m_tt_v : g.max_m_sf_v) <= 1.5f;
 }
 
-cudaError_t launch_nc(int dd, int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
+cudaError_t launch_nc(int kind, int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st) {
-    return dir == 0 ? launch_nc_fwd(dd, g, views, in_t, in, out_t, out, batch, st)
-                    : launch_nc_back(dd, g, views, in_t, in, out_t, out, batch, st);
+    return dir == 0 ? launch_nc_fwd(kind, g, views, in_t, in, out_t, out, batch, st)
+                    : launch_nc_back(kind, g, views, in_t, in, out_t, out, batch, st);
+}
+
+// SF-TT: the back direction scales the sinogram by each cell's amplitude into
+// a stream-ordered FP32 workspace first
+template <typename TIn>
+__global__ void __launch_bounds__(256)
+tt_prescale(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ y, float *__restrict__ yp,
+            int batch) {
+    const size_t nview_cells = (size_t)g.nv * g.nu;
+    const size_t total = nview_cells * g.nview * batch;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t % g.nu);
+        const int b = (int)((t / g.nu) % g.nv);
+        const int v = (int)((t / nview_cells) % g.nview);
+        yp[t] = tt_amp(views[v], g, a, b) * ld(y, t);
+    }
+}
+
+cudaError_t launch_sftt(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                        void *out, int batch, cudaStream_t st) {
+    if (dir == 0) return launch_nc(NC_TT, 0, g, views, in_t, in, out_t, out, batch, st);
+    const size_t n = (size_t)g.nview * g.nv * g.nu * batch;
+    float *yp = nullptr;
+    cudaError_t e = workspace_alloc((void **)&yp, n * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const size_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152u * 64u ? want : 152u * 64u);
+    switch (in_t) {
+    case 0: tt_prescale<float><<<blocks, 256, 0, st>>>(g, views, static_cast<const float *>(in), yp, batch); break;
+    case 1: tt_prescale<__half><<<blocks, 256, 0, st>>>(g, views, static_cast<const __half *>(in), yp, batch); break;
+    default:
+        tt_prescale<__nv_bfloat16><<<blocks, 256, 0, st>>>(g, views, static_cast<const __nv_bfloat16 *>(in), yp,
+                                                           batch);
+        break;
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_nc(NC_TT, 1, g, views, 0, yp, out_t, out, batch, st);
+    const cudaError_t ef = workspace_free(yp, st);
+    return e != cudaSuccess ? e : ef;
 }
 
 }  // namespace ctp

@@ -1,5 +1,6 @@
 // k_nc_fwd.cu -- forward projection of the non-circular SF-TR and DD
-// footprint projectors (the footprint and the dispatch are in k_nc.cuh).
+// footprint projectors and of SF-TT (the footprint and the dispatch are in
+// k_nc.cuh).
 #include "k_nc.cuh"
 
 namespace ctp {
@@ -82,7 +83,7 @@ template <int NA> struct NcCache {
 
 // Forward: CTA = 64 cells x 64 rows of one view, 256 threads; thread (tx, ty)
 // owns cells A0 + 4 tx .. + 3 and rows B0 + 4 ty .. + 3 (16 sums).
-template <typename TIn, bool DD, int NA, int NB>
+template <typename TIn, int KIND, int NA, int NB>
 __global__ void __launch_bounds__(256, 3)
 nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, const TIn *__restrict__ volZ,
        void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
@@ -100,7 +101,8 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
     const CtView &V = views[v];
     const int main_y = V.main_y;
     const SlabCoef sc = slab_coef(V, main_y);
-    const float mu = (DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad, mv = V.m_sf_v + 0.5f + kSearchPad;
+    const float mu = (KIND == NC_DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad;
+    const float mv = (KIND == NC_TT ? V.m_tt_v : V.m_sf_v) + 0.5f + kSearchPad;
     const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
     const size_t nvox = (size_t)g.nx * g.ny * g.nz;
     const TIn *x = vol + (size_t)bt * nvox;
@@ -136,7 +138,7 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
                     const int l = lc + idx / nkr, k = kc + idx % nkr;
                     const int i = main_y ? l : s, j = main_y ? s : l;
                     NcFp<NA, NB> P;
-                    nc_fp<DD, NA, NB>(V, g, i, j, k, P);
+                    nc_fp<KIND, NA, NB>(V, g, i, j, k, P);
                     const float xv = xz ? ld(xz, ((size_t)j * g.nx + i) * g.nz + k)
                                         : ld(x, ((size_t)k * g.ny + j) * g.nx + i);
                     const float w = P.amp * xv;
@@ -207,18 +209,18 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
             const int ac = a + c;
             if (ac < g.nu)
                 st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + ac,
-                       DD ? acc[r][c] * dd_len<false>(V, g, ac, b) : acc[r][c], out_t);
+                       KIND != NC_SF ? acc[r][c] * nc_cell_factor<KIND>(V, g, ac, b) : acc[r][c], out_t);
         }
     }
 }
 
 namespace {
-template <typename TIn, bool DD, int NA, int NB> struct NcFwd {
+template <typename TIn, int KIND, int NA, int NB> struct NcFwd {
     static cudaError_t go(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
                           cudaStream_t st) {
         const TIn *src = static_cast<const TIn *>(in);
         const size_t smem = sizeof(NcCache<NA>);
-        cudaError_t e = cudaFuncSetAttribute(nc_fwd<TIn, DD, NA, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(nc_fwd<TIn, KIND, NA, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         // a z-major copy of the volume (pooled workspace) makes each round's
@@ -234,7 +236,7 @@ template <typename TIn, bool DD, int NA, int NB> struct NcFwd {
         }
         const int tiles_u = (g.nu + 63) / 64, tiles_v = (g.nv + 63) / 64;
         dim3 blk(16, 16), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
-        nc_fwd<TIn, DD, NA, NB><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u, tiles_v);
+        nc_fwd<TIn, KIND, NA, NB><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u, tiles_v);
         e = cudaGetLastError();
         if (xZ) {
             const cudaError_t ef = workspace_free(xZ, st);
@@ -245,9 +247,9 @@ template <typename TIn, bool DD, int NA, int NB> struct NcFwd {
 };
 }  // namespace
 
-cudaError_t launch_nc_fwd(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+cudaError_t launch_nc_fwd(int kind, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                           void *out, int batch, cudaStream_t st) {
-    return nc_dispatch<NcFwd>(dd, in_t, g, views, in, out, out_t, batch, st);
+    return nc_dispatch<NcFwd>(kind, in_t, g, views, in, out, out_t, batch, st);
 }
 
 }  // namespace ctp
