@@ -22,12 +22,13 @@
  * stream-ordered workspace from a library-owned memory pool on the current
  * device (kept in the pool between calls, so steady-state calls do not reach
  * the driver's allocator) and return it on the same stream:
- *   ct_back with CT_DD: the sinogram scaled by each cell's path length,
- *     batch x nview x nv x nu floats;
+ *   ct_back with CT_DD or CT_SF_TT: the sinogram scaled by each cell's
+ *     path length or amplitude, batch x nview x nv x nu floats;
  *   ct_forward with CT_SF or CT_DD (circular geometry with nz a multiple
- *     of 4 and at least 8, or non-circular geometry) and with CT_VOXEL (the
- *     same circular cases): a z-major copy of the volume, batch x nz x ny x
- *     nx elements of in_t (skipped, at some speed, when it cannot be had).
+ *     of 4 and at least 8, or non-circular geometry), with CT_SF_TT, and
+ *     with CT_VOXEL (the same circular cases): a z-major copy of the volume,
+ *     batch x nz x ny x nx elements of in_t (skipped, at some speed, when it
+ *     cannot be had).
  * Results are deterministic: no atomics, fixed summation order.
  *
  * Errors: each call returns a ct_status; ct_last_error() gives a message for
@@ -167,8 +168,8 @@ ct_status ct_forward(const ct_geometry *geom, ct_projector proj, ct_mode mode,
  * sino: device pointer, batch x nview x nv x nu elements of type in_t.
  * vol:  device pointer, batch x nz x ny x nx elements of type out_t;
  *       overwritten.  Other arguments as for ct_forward.
- * CT_DD uses the pooled stream-ordered workspace of the threading note
- * above; CT_ERR_OOM when it cannot be had. */
+ * CT_DD and CT_SF_TT use the pooled stream-ordered workspace of the
+ * threading note above; CT_ERR_OOM when it cannot be had. */
 ct_status ct_back(const ct_geometry *geom, ct_projector proj, ct_mode mode,
                   ct_dtype in_t, const void *sino, ct_dtype out_t, void *vol,
                   int batch, void *cuda_stream);
