@@ -76,6 +76,7 @@ def _load():
             lib.oracle_set_threads.argtypes = [C.c_int]
             lib.oracle_ramp_filter.argtypes = [P(_Desc), d, d, C.c_int]
             lib.oracle_back_recon.argtypes = [P(_Desc), d, d, C.c_int]
+            lib.oracle_back_recon_proj.argtypes = [P(_Desc), C.c_int, d, d, C.c_int]
             lib.oracle_recon_dbeta.argtypes = [P(_Desc), C.c_int]
             lib.oracle_recon_dbeta.restype = C.c_double
             lib.oracle_max_threads.restype = C.c_int
@@ -234,22 +235,23 @@ def ramp_filter(spec: GeometrySpec, sino: np.ndarray) -> np.ndarray:
     return q[0] if squeeze else q
 
 
-def back_recon(spec: GeometrySpec, q: np.ndarray) -> np.ndarray:
-    """Recon-mode (depth-weighted, voxel-driven) backprojection of filtered
-    projections q: the second half of FBP."""
+def back_recon(spec: GeometrySpec, q: np.ndarray, projector: str = "voxel") -> np.ndarray:
+    """Recon-mode (depth-weighted) backprojection of filtered projections q:
+    the second half of FBP, with the voxel-driven bilinear interpolation or
+    the normalised DD / SF footprints."""
     lib = _load()
     g = _Geom(spec)
     y = np.ascontiguousarray(q, dtype=np.float64)
     squeeze = y.ndim == 3
     y = y.reshape((-1,) + _sino_shape(spec))
     x = np.zeros((y.shape[0],) + _vol_shape(spec))
-    lib.oracle_back_recon(g.ref(), _dptr(y), _dptr(x), y.shape[0])
+    lib.oracle_back_recon_proj(g.ref(), PROJECTORS[projector], _dptr(y), _dptr(x), y.shape[0])
     return x[0] if squeeze else x
 
 
-def fbp(spec: GeometrySpec, sino: np.ndarray) -> np.ndarray:
+def fbp(spec: GeometrySpec, sino: np.ndarray, projector: str = "voxel") -> np.ndarray:
     """Filtered backprojection: back_recon(ramp_filter(sino))."""
-    return back_recon(spec, ramp_filter(spec, sino))
+    return back_recon(spec, ramp_filter(spec, sino), projector)
 
 
 def recon_dbeta(spec: GeometrySpec, view: int) -> float:

@@ -819,9 +819,73 @@ int oracle_ramp_filter(const og_desc *g, const double *in, double *out, int batc
     return 0;
 }
 
-/* x = recon-mode backprojection of filtered projections q (Sec. 2.3), with
-   the voxel-driven (bilinear) interpolation: vol batch x nz x ny x nx */
+/* Recon-mode interpolation weights of the footprint projectors: the
+   projector's transaxial and axial footprints, each normalised to a unit
+   total (so they act as an interpolation kernel, like the bilinear hat):
+     DD: (overlap with [u-, u+]) / (u+ - u-) x (overlap with [v-, v+]) / (v+ - v-)
+     SF: (integral of the trapezoid over the cell) / (its area) x the same axial factor
+   with the boundary points / corners of fp_dd / fp_sf. */
+static void recon_fp(const og_desc *g, const og_frame *f, int proj, int v, int i, int j, int k, og_fp *fp)
+{
+    double X[3], P[3], tau[4], v1, v2, tmp;
+    fp->n = 0;
+    voxel_centre(g, v, i, j, k, X);
+    double dz = eff_dz(g), dv = eff_dv(g);
+    if (proj == OG_DD) {
+        int my = dd_main_is_y(f);
+        memcpy(P, X, sizeof P);
+        if (my) P[0] = X[0] - 0.5 * g->dx; else P[1] = X[1] - 0.5 * g->dy;
+        project(f, g->curved, P, &tau[0], &tmp);
+        memcpy(P, X, sizeof P);
+        if (my) P[0] = X[0] + 0.5 * g->dx; else P[1] = X[1] + 0.5 * g->dy;
+        project(f, g->curved, P, &tau[3], &tmp);
+        if (tau[0] > tau[3]) { tmp = tau[0]; tau[0] = tau[3]; tau[3] = tmp; }
+        tau[1] = tau[0];
+        tau[2] = tau[3];
+    } else {
+        int q = 0;
+        for (int sx = -1; sx <= 1; sx += 2)
+            for (int sy = -1; sy <= 1; sy += 2) {
+                P[0] = X[0] + 0.5 * sx * g->dx;
+                P[1] = X[1] + 0.5 * sy * g->dy;
+                P[2] = X[2];
+                project(f, g->curved, P, &tau[q++], &tmp);
+            }
+        sort4(tau);
+    }
+    memcpy(P, X, sizeof P); P[2] = X[2] - 0.5 * dz;
+    project(f, g->curved, P, &tmp, &v1);
+    memcpy(P, X, sizeof P); P[2] = X[2] + 0.5 * dz;
+    project(f, g->curved, P, &tmp, &v2);
+    double vlo = dmin(v1, v2), vhi = dmax(v1, v2);
+    double area = 0.5 * (tau[3] + tau[2] - tau[1] - tau[0]), height = vhi - vlo;
+    int a0, a1, b0, b1;
+    cell_range(tau[0], tau[3], g->du, g->nu, &a0, &a1);
+    cell_range(vlo, vhi, dv, g->nv, &b0, &b1);
+    for (int b = b0; b <= b1; ++b) {
+        double vc = cell_v(g, b);
+        double Fv = overlap(vlo, vhi, vc - 0.5 * dv, vc + 0.5 * dv) / height;
+        if (Fv == 0.0) continue;
+        for (int a = a0; a <= a1; ++a) {
+            double uc = cell_u(g, a);
+            double Fu = (trap_integral(tau, uc + 0.5 * g->du) - trap_integral(tau, uc - 0.5 * g->du)) / area;
+            if (Fu == 0.0) continue;
+            fp_push(fp, a, b, Fu * Fv);
+        }
+    }
+}
+
+/* x = recon-mode backprojection of filtered projections q (Sec. 2.3):
+   vol batch x nz x ny x nx.  proj: OG_VOXEL (bilinear interpolation) or
+   OG_DD / OG_SF (their normalised footprints, recon_fp). */
+int oracle_back_recon_proj(const og_desc *g, int proj, const double *q, double *vol, int batch);
+
 int oracle_back_recon(const og_desc *g, const double *q, double *vol, int batch)
+{
+    return oracle_back_recon_proj(g, OG_VOXEL, q, vol, batch);
+}
+
+int oracle_back_recon_proj(const og_desc *g, int proj, const double *q, double *vol, int batch)
 {
     int nz = nz_eff(g), nv = nv_eff(g);
     size_t view_sz = (size_t)nv * g->nu, sstride = view_sz * g->nview;
@@ -845,6 +909,17 @@ int oracle_back_recon(const og_desc *g, const double *q, double *vol, int batch)
             double w[3] = { X[0] - f->s[0], X[1] - f->s[1], X[2] - f->s[2] };
             double a = dot3(w, f->eu), c = dot3(w, f->n);
             double W = g->curved ? dbeta[v] / (a * a + c * c) : dbeta[v] * (-dot3(f->s, f->n)) * f->D / (c * c);
+            if (proj != OG_VOXEL) {
+                og_fp *fp = (og_fp *)malloc(sizeof(og_fp));
+                fp->overflow = 0;
+                recon_fp(g, f, proj, v, i, j, k, fp);
+                for (int t = 0; t < fp->n; ++t)
+                    for (int bt = 0; bt < batch; ++bt)
+                        vol[bt * vstride + vi] += W * fp->w[t] *
+                            q[bt * sstride + (size_t)v * view_sz + (size_t)fp->b[t] * g->nu + fp->a[t]];
+                free(fp);
+                continue;
+            }
             double fa = u / g->du + 0.5 * (g->nu - 1);
             double fb = (g->kind == 0) ? 0.0 : vv / g->dv + 0.5 * (nv - 1);
             int a0 = (int)floor(fa), b0 = (int)floor(fb);

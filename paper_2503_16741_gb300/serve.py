@@ -26,7 +26,7 @@ from typing import Any, Callable, Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-OPS = ("fwd", "back", "mbir")
+OPS = ("fwd", "back", "mbir", "fbp")
 ITEMSIZE = {"f32": 4, "f16": 2, "bf16": 2}
 
 
@@ -34,8 +34,10 @@ ITEMSIZE = {"f32": 4, "f16": 2, "bf16": 2}
 class Request:
     """One job.  `geometry`: keyword arguments of `Geometry` (hashable once
     frozen by `geometry_key`).  `data`: host array, the volume (fwd) or the
-    sinogram (back, mbir), shape (nz, ny, nx) / (nview, nv, nu) (2D: without
-    the z / v axis).  `dtype`: storage type on the device."""
+    sinogram (back, mbir, fbp), shape (nz, ny, nx) / (nview, nv, nu) (2D:
+    without the z / v axis).  `dtype`: storage type on the device.  `fbp`
+    reconstructs by filtered backprojection (the projector is the recon
+    mode's voxel-driven one whatever `projector` says)."""
     geometry: Dict[str, Any]
     op: str
     data: np.ndarray
@@ -64,7 +66,7 @@ def shapes(geom: Dict[str, Any]):
 
 def request_bytes(req: Request) -> int:
     """Device bytes a request holds while it runs: input, output and, for
-    MBIR, the residual sinogram."""
+    MBIR and FBP, the residual or filtered sinogram (FP32 for FBP)."""
     vol, sino = shapes(req.geometry)
     nv, ns = int(np.prod(vol)), int(np.prod(sino))
     it = ITEMSIZE[req.dtype]
@@ -72,6 +74,8 @@ def request_bytes(req: Request) -> int:
         return (nv + ns) * it
     if req.op == "back":
         return (ns + nv) * it
+    if req.op == "fbp":
+        return (ns + nv) * it + ns * 4
     return (2 * ns + nv) * it
 
 
@@ -320,7 +324,7 @@ class GpuExecutor(Executor):
         return self._lr[key]
 
     def launch(self, slot: int, reqs: Sequence[Request]):
-        from .binding import back_into, forward_into
+        from .binding import back_into, forward_into, ramp_filter
         from .mbir import ls_gradient_descent
         torch = self.torch
         torch.cuda.set_device(self.device)
@@ -337,6 +341,7 @@ class GpuExecutor(Executor):
         host_in = self._pinned_buffer((len(reqs),) + tuple(in_shape), dt)
         for k, r in enumerate(reqs):
             host_in[k].copy_(torch.from_numpy(np.asarray(r.data, dtype=np.float32)))
+        tmp = None  # a stream-ordered temporary that must outlive the launch
         with torch.cuda.stream(stream):
             d_in = host_in.to(self.device, non_blocking=True)
             if r0.op == "fwd":
@@ -345,6 +350,11 @@ class GpuExecutor(Executor):
             elif r0.op == "back":
                 d_out = torch.empty((len(reqs),) + vol, dtype=dt, device=self.device)
                 back_into(geom, d_in, d_out, r0.projector, stream=stream)
+            elif r0.op == "fbp":
+                tmp = torch.empty(d_in.shape, dtype=torch.float32, device=self.device)
+                ramp_filter(geom, d_in, out=tmp, stream=stream)
+                d_out = torch.empty((len(reqs),) + vol, dtype=dt, device=self.device)
+                back_into(geom, tmp, d_out, "voxel", mode="recon", stream=stream)
             else:
                 d_out = ls_gradient_descent(geom, d_in, r0.projector, r0.iters, lr=lr, stream=stream)
             host_out = self._pinned_buffer(tuple(d_out.shape), dt)
@@ -352,7 +362,7 @@ class GpuExecutor(Executor):
             ev = torch.cuda.Event()
             ev.record(stream)
         # keep device buffers alive until the event has passed
-        return {"event": ev, "host_out": host_out, "host_in": host_in, "keep": (d_in, d_out)}
+        return {"event": ev, "host_out": host_out, "host_in": host_in, "keep": (d_in, d_out, tmp)}
 
     def done(self, handle) -> bool:
         return handle["event"].query()

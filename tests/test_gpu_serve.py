@@ -36,9 +36,9 @@ def test_results_alone_equal_results_in_the_mix(ct):
              ragged("noncirc3d", "flat", 44)]
     rng = np.random.default_rng(0)
     reqs = []
-    for k in range(24):
+    for k in range(32):
         sp = specs[k % 4]
-        op = ["fwd", "back", "mbir"][k % 3]
+        op = ["fwd", "back", "mbir", "fbp"][k % 4 if k >= 24 else k % 3]
         proj = ["sf", "dd", "voxel", "ray"][(k // 3) % 4]
         vol = (sp.ny, sp.nx) if sp.kind == "fan2d" else sp.vol_shape
         sino = (sp.nview, sp.nu) if sp.kind == "fan2d" else sp.sino_shape
@@ -58,6 +58,8 @@ def test_results_alone_equal_results_in_the_mix(ct):
             alone = ct.forward(g, d, r.projector)
         elif r.op == "back":
             alone = ct.back(g, d, r.projector)
+        elif r.op == "fbp":
+            alone = ct.fbp(g, d)
         else:
             lr = srv.ex.step_size(r.geometry, r.projector)
             alone = ls_gradient_descent(g, d, r.projector, r.iters, lr=lr)

@@ -44,7 +44,7 @@ class FakeExecutor(Executor):
     def results(self, h):
         with self.lock:
             self.active -= 1
-        return [2 * r.data + ["fwd", "back", "mbir"].index(r.op) for r in h["reqs"]]
+        return [2 * r.data + ["fwd", "back", "mbir", "fbp"].index(r.op) for r in h["reqs"]]
 
 
 def req(geom, op, seed=0, **kw):
@@ -152,6 +152,16 @@ def test_launch_failure_is_reported_and_frees_resources():
     good.result(timeout=5)
     s.close()
     assert s.in_use == 0
+
+
+def test_fbp_requests_are_accepted_and_sized():
+    from paper_2503_16741_gb300.serve import request_bytes
+    r = Request(G2, "fbp", np.zeros((4, 16)), dtype="f16")
+    vol, sino = 8 * 8, 4 * 16  # G2: 8 x 8 image, 4 views x 16 cells
+    assert request_bytes(r) == (sino + vol) * 2 + sino * 4  # plus the FP32 filtered sinogram
+    s = Scheduler(FakeExecutor(), hbm_budget=1 << 30)
+    assert s.submit(r).result(timeout=5) is not None
+    s.close()
 
 
 def test_unknown_op_is_rejected():
