@@ -66,15 +66,18 @@ typedef enum {
 /* Projection modes (Sec. 2.3): "proj" is the matched pair; "recon" is the
    backprojection of filtered backprojection (FBP), which carries a
    depth-dependent weighting instead of the projector's own weights (after
-   Kak & Slaney 2001): ct_back with CT_VOXEL backprojects ramp-filtered
-   projections (ct_ramp_filter) with bilinear interpolation and the weight
+   Kak & Slaney 2001): ct_back backprojects ramp-filtered projections
+   (ct_ramp_filter), interpolating with the voxel-driven bilinear hat
+   (CT_VOXEL) or with the DD / SF-TR footprints normalised to a unit total
+   (CT_DD, CT_SF; non-circular footprints of at most 8 cells x 4 rows), and
+   weighting each view by
      flat detector:   dbeta R D / ((X - s).n)^2
      curved detector: dbeta / rho^2,  rho = distance of X from the source axis
    where D is the source-detector distance (flat) or detector radius (curved),
    R = (O - s).n the source's distance to the rotation centre O = 0 along the
    detector normal, and dbeta the view's share of the gantry angle (half the
    angular gaps to the nearest distinct view angles on either side;
-   2 pi / nview for pose-given geometries).  Other projectors, and
+   2 pi / nview for pose-given geometries).  CT_RAY and CT_SF_TT, and
    ct_forward, return CT_ERR_UNSUPPORTED in recon mode. */
 typedef enum { CT_MODE_PROJ = 0, CT_MODE_RECON = 1 } ct_mode;
 

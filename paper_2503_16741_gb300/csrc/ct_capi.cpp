@@ -364,8 +364,8 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");
     if (proj < CT_VOXEL || proj > CT_SF_TT) return fail(CT_ERR_INVALID_ARG, "unknown projector");
     if (mode != CT_MODE_PROJ && mode != CT_MODE_RECON) return fail(CT_ERR_INVALID_ARG, "unknown mode");
-    if (mode == CT_MODE_RECON && (dir != 1 || proj != CT_VOXEL))
-        return fail(CT_ERR_UNSUPPORTED, "recon mode is the voxel-driven FBP backprojection (ct_back, CT_VOXEL)");
+    if (mode == CT_MODE_RECON && (dir != 1 || (proj != CT_VOXEL && proj != CT_DD && proj != CT_SF)))
+        return fail(CT_ERR_UNSUPPORTED, "recon mode is the FBP backprojection (ct_back) of CT_VOXEL, CT_DD, CT_SF");
     if (in_t < CT_F32 || in_t > CT_BF16 || out_t < CT_F32 || out_t > CT_BF16)
         return fail(CT_ERR_INVALID_ARG, "unknown dtype");
     if (!in || !out) return fail(CT_ERR_INVALID_ARG, "null data pointer");
@@ -393,9 +393,10 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     G.alpha = alpha;
     G.beta = beta;
     cudaError_t e;
-    if (mode == CT_MODE_RECON) proj = CT_VOXEL;
-    switch (mode == CT_MODE_RECON ? -1 : (int)proj) {
-    case -1: e = ctp::launch_voxel_recon(G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    switch (mode == CT_MODE_RECON ? -1 - (int)proj : (int)proj) {
+    case -1 - CT_VOXEL: e = ctp::launch_voxel_recon(G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    case -1 - CT_DD: e = ctp::launch_recon_fp(1, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
+    case -1 - CT_SF: e = ctp::launch_recon_fp(0, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_VOXEL: e = ctp::launch_voxel(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_RAY: e = ctp::launch_ray(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     case CT_DD: e = ctp::launch_dd(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
@@ -403,6 +404,8 @@ static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mo
     default: e = ctp::launch_sf(dir, G, g->dev_views, in_t, in, out_t, out, batch, s); break;
     }
     if (e == cudaErrorMemoryAllocation) return fail(CT_ERR_OOM, "workspace allocation failed");
+    if (e == cudaErrorNotSupported)
+        return fail(CT_ERR_UNSUPPORTED, "recon mode: non-circular footprints wider than 8 cells x 4 rows");
     if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return CT_OK;
 }

@@ -30,6 +30,12 @@ cudaError_t launch_vx_fwd_circ(const CtGrid &g, const CtView *views, int in_t, c
 // depth-weighted voxel-driven backprojection of the filtered projections
 cudaError_t launch_ramp_filter(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                                void *out, int batch, cudaStream_t st);
+// recon mode with the normalised DD (dd = 1) or SF-TR (dd = 0) footprints;
+// non-circular footprints beyond 8 x 4 give cudaErrorNotSupported
+cudaError_t launch_recon_fp(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                            void *out, int batch, cudaStream_t st);
+cudaError_t launch_nc_recon(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                            void *out, int batch, cudaStream_t st);
 cudaError_t launch_voxel_recon(const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                                void *out, int batch, cudaStream_t st);
 cudaError_t launch_voxel(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,

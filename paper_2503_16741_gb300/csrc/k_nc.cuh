@@ -38,6 +38,8 @@ template <int NA, int NB> struct NcFp {
     float Fu[NA];  // transaxial weights of cells a0 .. a0 + NA - 1
     float Fv[NB];  // axial weights of rows b0 .. b0 + NB - 1
     float amp;     // SF-TR amplitude dx |w| / max(|w_x|, |w_y|); DD, SF-TT: 1 (their factor is per cell)
+    float cn;      // depth (X - s).n of the voxel centre
+    float size;    // SF-TR, DD: transaxial area (cells) x axial height (rows) of the footprint
 };
 
 // Trapezoid with the ramp factors formed by a fast reciprocal (relative
@@ -154,7 +156,9 @@ __device__ __forceinline__ void nc_fp(const CtView &V, const CtGrid &g, int i, i
             P.Fv[q] = overlap(vlo, vhi, e - 0.5f, e + 0.5f);
         }
         P.b0 = bref + e0;
+        P.size = 0.5f * ((T.k3 - T.k0) + (T.k2 - T.k1)) * (vhi - vlo);
     }
+    P.cn = cn;
     if (KIND != NC_SF) {
         P.amp = 1.f;
     } else {

@@ -14,7 +14,10 @@ constexpr int kNcViews = 16;
 // runs over its voxels one at a time (the per-voxel body appears once in the
 // code, which keeps the kernel within the instruction cache) with the
 // voxel's sum carried in shared memory between rounds.
-template <typename TIn, int KIND, int NA, int NB, int ZT>
+// RECON: the recon-mode (FBP) backprojection with the normalised footprint
+// as the interpolation: weight rc_w / depth^2 over the footprint's area x
+// height (SF-TR and DD).
+template <typename TIn, int KIND, int NA, int NB, int ZT, bool RECON = false>
 __global__ void __launch_bounds__(128, 8)
 nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino, void *__restrict__ vol,
         int out_t, int tiles_x, int nzc) {
@@ -80,7 +83,7 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
                         s = fmaf(P.Fv[q], rs, s);
                     }
                 }
-                a = fmaf(P.amp, s, a);
+                a = fmaf(RECON ? V.rc_w / (P.cn * P.cn * P.size) : P.amp, s, a);
             }
             acc[kk][tid] = a;
         }
@@ -107,6 +110,25 @@ template <typename TIn, int KIND, int NA, int NB> struct NcBack {
     }
 };
 }  // namespace
+
+template <typename TIn, int KIND, int NA, int NB> struct NcBackRecon {
+    static cudaError_t go(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
+                          cudaStream_t st) {
+        constexpr int ZT = 8;
+        const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + ZT - 1) / ZT;
+        dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+        nc_back<TIn, KIND, NA, NB, ZT, true><<<grd, blk, 0, st>>>(g, views, static_cast<const TIn *>(in), out,
+                                                                  out_t, tiles_x, nzc);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_nc_recon(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                            void *out, int batch, cudaStream_t st) {
+    const int kind = dd ? NC_DD : NC_SF;
+    if (!nc_footprint_fits(g, kind)) return cudaErrorNotSupported;
+    return nc_dispatch<NcBackRecon>(kind, in_t, g, views, in, out, out_t, batch, st);
+}
 
 cudaError_t launch_nc_back(int kind, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                            void *out, int batch, cudaStream_t st) {

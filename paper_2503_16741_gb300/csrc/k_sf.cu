@@ -143,7 +143,11 @@ __device__ __forceinline__ float fp_amp(const C_ &C, float wz) {
     return DD ? 1.f : sf_amp_fast(C.invm, C.rxy2, wz);
 }
 
-template <typename TIn, bool CURVED, bool DD, int ZT>
+// RECON: the recon-mode (FBP) backprojection of filtered projections with the
+// normalised footprints as the interpolation (Sec. 2.3): the voxel's weight
+// is the depth weight rc_w / depth^2 over the footprint's transaxial area
+// (cells) and axial height (rows), constant down a column.
+template <typename TIn, bool CURVED, bool DD, int ZT, bool RECON = false>
 __global__ void __launch_bounds__(128, 7)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
@@ -182,6 +186,15 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             d0 = max(d0, -C.aref);
             d1 = min(d1, g.nu - 1 - C.aref);
             if (d0 > d1) continue;
+            float rw = 0.f;
+            if (RECON) {
+                const float fi = (float)i, fj = (float)j;
+                const float cu = fmaf(V.au[0], fi, fmaf(V.au[1], fj, V.au[3]));
+                const float cn = fmaf(V.an[0], fi, fmaf(V.an[1], fj, V.an[3]));
+                const float den2 = CURVED ? fmaf(cu, cu, cn * cn) : cn * cn;
+                const float area = 0.5f * ((C.T.k3 - C.T.k0) + (C.T.k2 - C.T.k1));
+                rw = V.rc_w / (den2 * area * (2.f * C.hv));
+            }
             const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
             if (d1 - d0 <= 3 && C.hv < 0.5f && C.sv > 0.f && g.nu >= 4) {
                 float F[4];
@@ -229,7 +242,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                         float Fv0, Fv1;
                         two_rows(rel - C.hv, rel + C.hv, e0, Fv0, Fv1);
                         const float wz = fmaf(fk, g.dz, V.o[2]);
-                        acc[kk] = fmaf(fp_amp<DD>(C, wz), fmaf(Fv0, Rs[e0 + 1][tid], Fv1 * Rs[e0 + 2][tid]),
+                        acc[kk] = fmaf(RECON ? rw : fp_amp<DD>(C, wz), fmaf(Fv0, Rs[e0 + 1][tid], Fv1 * Rs[e0 + 2][tid]),
                                        acc[kk]);
                     }
                 }
@@ -260,7 +273,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                         s = fmaf(Fv, r, s);
                     }
                     const float wz = fmaf((float)k, g.dz, V.o[2]);
-                    Gs[kk][tid] = fmaf(fp_amp<DD>(C, wz), s, Gs[kk][tid]);
+                    Gs[kk][tid] = fmaf(RECON ? rw : fp_amp<DD>(C, wz), s, Gs[kk][tid]);
                 }
             }
         }
@@ -802,12 +815,12 @@ cudaError_t fp_fwd_circ(const CtGrid &g, const CtView *views, const TIn *src, vo
     return cudaGetLastError();
 }
 
-template <typename TIn, bool CURVED, bool DD>
+template <typename TIn, bool CURVED, bool DD, bool RECON = false>
 cudaError_t fp_back_circ(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                          int batch, cudaStream_t st) {
     const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
     dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-    sf_back_circ<TIn, CURVED, DD, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    sf_back_circ<TIn, CURVED, DD, kZT, RECON><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     return cudaGetLastError();
 }
 
@@ -922,6 +935,30 @@ cudaError_t vx_fwd_t(const CtGrid &g, const CtView *views, const void *in, void 
                   : fp_fwd_stream<TIn, false, false, 1, 2, true>(g, views, src, out, out_t, batch, st);
 }
 }  // namespace
+
+namespace {
+template <typename TIn>
+cudaError_t recon_fp_t(int dd, const CtGrid &g, const CtView *views, const void *in, void *out, int out_t,
+                       int batch, cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    const bool curved = g.variant == GEO_CIRC_CURVED;
+    if (dd)
+        return curved ? fp_back_circ<TIn, true, true, true>(g, views, src, out, out_t, batch, st)
+                      : fp_back_circ<TIn, false, true, true>(g, views, src, out, out_t, batch, st);
+    return curved ? fp_back_circ<TIn, true, false, true>(g, views, src, out, out_t, batch, st)
+                  : fp_back_circ<TIn, false, false, true>(g, views, src, out, out_t, batch, st);
+}
+}  // namespace
+
+cudaError_t launch_recon_fp(int dd, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                            void *out, int batch, cudaStream_t st) {
+    if (g.variant == GEO_NONCIRC_FLAT) return launch_nc_recon(dd, g, views, in_t, in, out_t, out, batch, st);
+    switch (in_t) {
+    case 0: return recon_fp_t<float>(dd, g, views, in, out, out_t, batch, st);
+    case 1: return recon_fp_t<__half>(dd, g, views, in, out, out_t, batch, st);
+    default: return recon_fp_t<__nv_bfloat16>(dd, g, views, in, out, out_t, batch, st);
+    }
+}
 
 cudaError_t zmajor_copy(int elem_bytes, const void *x, void *xZ, int nx, int ny, int nz, int batch,
                         cudaStream_t st) {

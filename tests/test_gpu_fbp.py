@@ -41,13 +41,14 @@ def test_ramp_filter_matches_oracle(ct, kind, det, data):
     assert rel_l2(q.cpu().numpy().reshape(ref.shape), ref) <= TOL_F32
 
 
+@pytest.mark.parametrize("proj", ["voxel", "dd", "sf"])
 @pytest.mark.parametrize("kind,det", GEOMS)
-def test_recon_backprojection_matches_oracle(ct, kind, det):
+def test_recon_backprojection_matches_oracle(ct, kind, det, proj):
     spec = ragged(kind, det, seed=51)
     q = oracle.ramp_filter(spec, oracle.forward(spec, "dd", W.phantom(spec, seed=3)))
-    ref = oracle.back_recon(spec, q)
+    ref = oracle.back_recon(spec, q, proj)
     g = ct.Geometry.from_spec(spec)
-    x = ct.back(g, torch.as_tensor(q.reshape(_sino_shape(spec)), dtype=torch.float32).cuda(), "voxel",
+    x = ct.back(g, torch.as_tensor(q.reshape(_sino_shape(spec)), dtype=torch.float32).cuda(), proj,
                 mode="recon")
     assert rel_l2(x.cpu().numpy().reshape(ref.shape), ref) <= TOL_F32
 
@@ -101,13 +102,33 @@ def test_half_storage_fbp(ct):
     assert storage <= 5 * 2.0 ** -11, storage
 
 
-def test_recon_mode_is_the_voxel_driven_backprojection_only(ct):
+def test_recon_mode_is_a_backprojection_of_voxel_dd_or_sf(ct):
     spec = ragged("circ3d", "flat", seed=54)
     g = ct.Geometry.from_spec(spec)
     x = torch.rand(spec.vol_shape, device="cuda")
     y = torch.rand(spec.sino_shape, device="cuda")
-    with pytest.raises(ct.CTError):
-        ct.forward(g, x, "voxel", mode="recon")
-    for proj in ("sf", "dd", "ray"):
+    for proj in ("voxel", "sf"):
+        with pytest.raises(ct.CTError):
+            ct.forward(g, x, proj, mode="recon")
+    for proj in ("ray", "sftt"):
         with pytest.raises(ct.CTError):
             ct.back(g, y, proj, mode="recon")
+
+
+@pytest.mark.parametrize("proj", ["dd", "sf"])
+def test_footprint_fbp_reconstructs_the_gaussian_cylinder(ct, proj):
+    from test_oracle_fbp import _gauss_cyl_sino, _uneven_angles
+    nx, nz, nview, mu, sigma, c = 48, 24, 180, 0.02, 5.0, (8.0, -5.0)
+    spec = W.GeometrySpec("circ3d", "flat", nx, nx, nz, 1.0, 1.0, 1.0, 160, 96, 0.8, 1.0, nview,
+                          theta=_uneven_angles(nview), sad=200.0, sdd=400.0, u_ofst=8.0, v_ofst=15.0)
+    y = _gauss_cyl_sino(spec, (c[0], c[1], 0.0), sigma, mu)
+    g = ct.Geometry.from_spec(spec)
+    q = ct.ramp_filter(g, torch.as_tensor(y, dtype=torch.float32).cuda())
+    x = ct.back(g, q, proj, mode="recon").cpu().numpy()
+    ref_o = oracle.fbp(spec, y, proj)
+    assert rel_l2(x, ref_o) <= TOL_F32
+    g_ = np.arange(nx) - 0.5 * (nx - 1)
+    yy, xx = np.meshgrid(g_, g_, indexing="ij")
+    ref = mu * np.exp(-((xx - c[0]) ** 2 + (yy - c[1]) ** 2) / (2 * sigma ** 2))
+    roi = np.hypot(xx, yy) < 20
+    assert max(np.abs(x[k] - ref)[roi].max() for k in range(nz)) < 0.01 * mu
