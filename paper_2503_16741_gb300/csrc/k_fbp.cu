@@ -13,22 +13,31 @@
 // host: the bracket is small where the row is smooth, so FP32 does not lose
 // the digits that the large, nearly cancelling taps would cost.
 // One CTA per detector row; the row (zero-padded on both sides) and the
-// kernel's odd taps sit in shared memory.
+// kernel's odd taps sit in shared memory; a thread computes four outputs two
+// cells apart, sharing their samples along a sliding window.
+#include <algorithm>
+
 #include "ct_device.cuh"
 #include "ct_launch.h"
 
 namespace ctp {
 
 constexpr int kRampThreads = 256;
+constexpr int kRampR = 4;  // outputs per thread, two cells apart
 
+// A thread computes the outputs m0, m0 + 2, m0 + 4, m0 + 6: the taps of
+// outputs two cells apart share their samples, so stepping through the odd
+// taps slides a window of loaded samples along the row (two new loads per
+// tap instead of eight).  Each output's sum is formed exactly as in the
+// one-output form (same terms, same order: far taps first).
 template <typename TIn, bool CURVED>
 __global__ void __launch_bounds__(kRampThreads)
 ramp_rows(CtGrid g, const CtView *__restrict__ views, const TIn *in, void *out, int out_t) {
     // (in may equal out: a row is read whole into shared memory before it is written)
     extern __shared__ float sm[];
     const int nu = g.nu;
-    float *pw = sm + nu;          // pw[-nu .. 2 nu) valid, zero outside [0, nu)
-    float *hk = sm + 3 * nu;      // hk[j] = h(2 j + 1)
+    float *pw = sm + nu;          // pw[-nu .. 2 nu + 2 kRampR) valid, zero outside [0, nu)
+    float *hk = sm + 3 * nu + 2 * kRampR;  // hk[j] = h(2 j + 1)
     const int nodd = nu / 2;      // odd offsets 1, 3, .., < nu
     const size_t row = blockIdx.x;
     const int b = (int)(row % g.nv);
@@ -46,6 +55,7 @@ ramp_rows(CtGrid g, const CtView *__restrict__ views, const TIn *in, void *out, 
         pw[n - nu] = 0.f;
         pw[n + nu] = 0.f;
     }
+    for (int n = threadIdx.x; n < 2 * kRampR; n += blockDim.x) pw[2 * nu + n] = 0.f;
     constexpr float kInv2Pi2 = 0.05066059182116889f;  // 1 / (2 pi^2)
     for (int j = threadIdx.x; j < nodd; j += blockDim.x) {
         const float k = (float)(2 * j + 1);
@@ -58,14 +68,36 @@ ramp_rows(CtGrid g, const CtView *__restrict__ views, const TIn *in, void *out, 
         hk[j] = -kInv2Pi2 / (d * d);
     }
     __syncthreads();
-    for (int m = threadIdx.x; m < nu; m += blockDim.x) {
-        const float p0 = pw[m], two_p0 = 2.f * p0;
-        float acc = 0.f;
-        for (int j = nodd - 1; j >= 0; --j) {  // far taps (the small ones) first
-            const int k = 2 * j + 1;
-            acc = fmaf(hk[j], (pw[m - k] + pw[m + k]) - two_p0, acc);
+    const int nthr = (nu + 2 * kRampR - 1) / (2 * kRampR) * 2;  // threads that cover the row
+    for (int t = threadIdx.x; t < nthr; t += blockDim.x) {
+        const int m0 = (t >> 1) * 2 * kRampR + (t & 1);
+        float p0x2[kRampR], acc[kRampR], wm[kRampR], wp[kRampR];
+        const int k0 = 2 * nodd - 1;  // the farthest odd tap
+#pragma unroll
+        for (int r = 0; r < kRampR; ++r) {
+            p0x2[r] = 2.f * pw[m0 + 2 * r];
+            acc[r] = 0.f;
+            wm[r] = pw[m0 + 2 * r - k0];
+            wp[r] = pw[m0 + 2 * r + k0];
         }
-        st(out, row * nu + m, fmaf(step, acc, V.rc_c * p0), out_t);
+        for (int j = nodd - 1; j >= 0; --j) {  // far taps (the small ones) first
+            const float h = hk[j];
+#pragma unroll
+            for (int r = 0; r < kRampR; ++r) acc[r] = fmaf(h, (wm[r] + wp[r]) - p0x2[r], acc[r]);
+            if (j == 0) break;
+            const int k = 2 * j - 1;  // the next tap: the window moves two cells inwards
+#pragma unroll
+            for (int r = 0; r < kRampR - 1; ++r) wm[r] = wm[r + 1];
+            wm[kRampR - 1] = pw[m0 + 2 * (kRampR - 1) - k];
+#pragma unroll
+            for (int r = kRampR - 1; r > 0; --r) wp[r] = wp[r - 1];
+            wp[0] = pw[m0 + k];
+        }
+#pragma unroll
+        for (int r = 0; r < kRampR; ++r) {
+            const int m = m0 + 2 * r;
+            if (m < nu) st(out, row * nu + m, fmaf(step, acc[r], V.rc_c * (0.5f * p0x2[r])), out_t);
+        }
     }
 }
 
@@ -73,18 +105,21 @@ namespace {
 template <typename TIn>
 cudaError_t ramp_t(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
                    cudaStream_t s) {
-    const size_t smem = sizeof(float) * (3 * (size_t)g.nu + g.nu / 2 + 1);
+    const size_t smem = sizeof(float) * (3 * (size_t)g.nu + 2 * kRampR + g.nu / 2 + 1);
     const TIn *src = static_cast<const TIn *>(in);
     const unsigned rows = (unsigned)((size_t)g.nv * g.nview * batch);
+    // as many threads as the row's output groups need (whole warps, 64 .. 256)
+    const int groups = (g.nu + 2 * kRampR - 1) / (2 * kRampR) * 2;
+    const unsigned threads = (unsigned)std::min(kRampThreads, std::max(64, (groups + 31) / 32 * 32));
     cudaError_t e;
     if (g.variant == GEO_CIRC_CURVED) {
         e = cudaFuncSetAttribute(ramp_rows<TIn, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        ramp_rows<TIn, true><<<rows, kRampThreads, smem, s>>>(g, views, src, out, out_t);
+        ramp_rows<TIn, true><<<rows, threads, smem, s>>>(g, views, src, out, out_t);
     } else {
         e = cudaFuncSetAttribute(ramp_rows<TIn, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        ramp_rows<TIn, false><<<rows, kRampThreads, smem, s>>>(g, views, src, out, out_t);
+        ramp_rows<TIn, false><<<rows, threads, smem, s>>>(g, views, src, out, out_t);
     }
     return cudaGetLastError();
 }
