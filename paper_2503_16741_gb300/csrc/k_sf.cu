@@ -357,7 +357,7 @@ sf_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ s
 // no atomics.  Used when every footprint spans at most 4 cells (decided on
 // the host from the per-view footprint bound); otherwise sf_fwd_circ_wide.
 constexpr int kItems = 256;
-constexpr int kSlabSeg = 1024;
+constexpr int kSlabSeg = 256;
 
 template <int RPT, int NA> struct SfFwdSmem {
     float Z[8 * RPT][kItems];  // [row][item]: conflict-free in both stages
@@ -414,8 +414,9 @@ __device__ __forceinline__ void vx_stage1(const CtView &V, const CtGrid &g, int 
     }
 }
 
+// (with up to 4 cells per item the kernel fits 80 registers: 3 blocks per SM)
 template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, NA <= 4 ? 3 : 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
             const TIn *__restrict__ volZ, void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
     constexpr int BV = 8 * RPT;
