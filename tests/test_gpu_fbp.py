@@ -132,3 +132,18 @@ def test_footprint_fbp_reconstructs_the_gaussian_cylinder(ct, proj):
     ref = mu * np.exp(-((xx - c[0]) ** 2 + (yy - c[1]) ** 2) / (2 * sigma ** 2))
     roi = np.hypot(xx, yy) < 20
     assert max(np.abs(x[k] - ref)[roi].max() for k in range(nz)) < 0.01 * mu
+
+
+def test_fbp_batches_are_independent(ct):
+    spec = ragged("circ3d", "curved", seed=55)
+    g = ct.Geometry.from_spec(spec)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    y = torch.rand((2, 3) + spec.sino_shape, generator=gen, device="cuda")
+    x = ct.fbp(g, y)
+    for b in range(2):
+        for c in range(3):
+            assert torch.equal(x[b, c], ct.fbp(g, y[b, c].contiguous()))
+    q = ct.ramp_filter(g, y)
+    for proj in ("dd", "sf"):
+        xb = ct.back(g, q, proj, mode="recon")
+        assert torch.equal(xb[1, 2], ct.back(g, q[1, 2].contiguous(), proj, mode="recon"))
