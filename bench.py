@@ -41,8 +41,8 @@ N_SM, FP32_LANES = 152, 128
 # DRAM bytes per launch from one ncu capture of the same kernel source
 # (sha256 of the .cu at capture time); null once the source changes.
 NCU_TRAFFIC = {
-    "sf_back": {"bytes": 419.8e6, "src": "72e3cec8c7de7156"},
-    "sf_fwd": {"bytes": 945.8e6, "src": "72e3cec8c7de7156"},
+    "sf_back": {"bytes": 417.7e6, "src": "06c6fc1164c1c85b"},
+    "sf_fwd": {"bytes": 917.9e6, "src": "06c6fc1164c1c85b"},
 }
 
 

@@ -21,6 +21,13 @@ cudaError_t launch_dd_nc(int dir, const CtGrid &g, const CtView *views, int in_t
 bool nc_footprint_fits(const CtGrid &g, int kind);
 cudaError_t launch_sftt(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                         void *out, int batch, cudaStream_t st);
+// SF-TT in circular flat 3D geometry on the streaming forward and the
+// column-walk back (k_sf.cu), for transaxial footprints of at most 8 cells and
+// axial ones of at most 4 rows; the back direction takes the FP32 sinogram
+// already scaled by the per-cell amplitude (in_t ignored).
+bool sftt_circ_fits(const CtGrid &g);
+cudaError_t launch_sftt_circ(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                             void *out, int batch, cudaStream_t st);
 cudaError_t launch_nc(int kind, int dir, const CtGrid &g, const CtView *views, int in_t, const void *in,
                       int out_t, void *out, int batch, cudaStream_t st);
 // voxel-driven forward in circular geometry (the streaming forward of k_sf.cu)

@@ -148,7 +148,9 @@ cudaError_t launch_nc(int kind, int dir, const CtGrid &g, const CtView *views, i
 }
 
 // SF-TT: the back direction scales the sinogram by each cell's amplitude into
-// a stream-ordered FP32 workspace first
+// a stream-ordered FP32 workspace first.  Circular flat 3D geometry takes the
+// column-walk kernels of k_sf.cu (the transaxial footprint is reused down
+// each column), every other flat geometry the per-voxel footprint kernels.
 template <typename TIn>
 __global__ void __launch_bounds__(256)
 tt_prescale(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ y, float *__restrict__ yp,
@@ -165,7 +167,10 @@ tt_prescale(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
 
 cudaError_t launch_sftt(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
                         void *out, int batch, cudaStream_t st) {
-    if (dir == 0) return launch_nc(NC_TT, 0, g, views, in_t, in, out_t, out, batch, st);
+    const bool circ = sftt_circ_fits(g);
+    if (dir == 0)
+        return circ ? launch_sftt_circ(0, g, views, in_t, in, out_t, out, batch, st)
+                    : launch_nc(NC_TT, 0, g, views, in_t, in, out_t, out, batch, st);
     const size_t n = (size_t)g.nview * g.nv * g.nu * batch;
     float *yp = nullptr;
     cudaError_t e = workspace_alloc((void **)&yp, n * sizeof(float), st);
@@ -181,7 +186,9 @@ cudaError_t launch_sftt(int dir, const CtGrid &g, const CtView *views, int in_t,
         break;
     }
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_nc(NC_TT, 1, g, views, 0, yp, out_t, out, batch, st);
+    if (e == cudaSuccess)
+        e = circ ? launch_sftt_circ(1, g, views, 0, yp, out_t, out, batch, st)
+                 : launch_nc(NC_TT, 1, g, views, 0, yp, out_t, out, batch, st);
     const cudaError_t ef = workspace_free(yp, st);
     return e != cudaSuccess ? e : ef;
 }

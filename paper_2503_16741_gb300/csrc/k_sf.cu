@@ -18,6 +18,7 @@
 
 #include "ct_device.cuh"
 #include "ct_launch.h"
+#include "k_nc.cuh"
 
 namespace ctp {
 
@@ -72,6 +73,64 @@ __device__ __forceinline__ SfCol sf_col(const CtView &V, const CtGrid &g, int i,
 __device__ __forceinline__ float sf_amp(const SfCol &C, const CtGrid &g, const CtView &V, int k) {
     const float wz = fmaf((float)k, g.dz, V.o[2]);
     return C.invm * sqrtf(fmaf(wz, wz, C.rxy2));
+}
+
+// SF-TT in circular flat geometry (the transaxial footprint is SF-TR's): the
+// axial trapezoid of voxel k has its knots on the z faces at the column's
+// transaxial corners nearest to and farthest from the source (against the
+// normal's transaxial components; a component below 1e-7 of the voxel size
+// counts as zero and takes the negative side).  A corner at depth cn (1 + e)^-1
+// projects the voxel's centre to fv(k) + g(k) e and its z faces to -+ hv (1 + e)
+// about that, with g(k) = fv(k) - Cv = sv k + g0 linear in k.
+struct TtCol {
+    float g0;
+    float eN, eF;  // nearest, farthest corner: cn / depth - 1
+    float hN, hF;  // half heights hv (1 + e)
+};
+
+__device__ __forceinline__ TtCol tt_col(const CtView &V, const CtGrid &g, const SfCol &C, int i, int j) {
+    const float cn = fmaf(V.an[0], (float)i, fmaf(V.an[1], (float)j, V.an[3]));
+    const float eps = 1e-7f * g.dx;
+    const float hxn = 0.5f * V.an[0], hyn = 0.5f * V.an[1];
+    const float nn = (V.an[0] < -eps ? hxn : -hxn) + (V.an[1] < -eps ? hyn : -hyn);
+    const float fn = (V.an[0] > eps ? hxn : -hxn) + (V.an[1] > eps ? hyn : -hyn);
+    TtCol T;
+    T.eN = -nn / (cn + nn);
+    T.eF = -fn / (cn + fn);
+    T.hN = fmaf(C.hv, T.eN, C.hv);
+    T.hF = fmaf(C.hv, T.eF, C.hv);
+    T.g0 = (V.Kv / cn) * V.av[3];
+    return T;
+}
+
+// rows e0 .. e0 + 3 (relative to the row of the voxel centre, whose offset
+// in it is vf) under the axial trapezoid of voxel fk, and their weights
+// (zero past the trapezoid; it spans at most 4 rows when its half height
+// bound is at most 1.5 rows)
+__device__ __forceinline__ void tt_rows(const SfCol &C, const TtCol &T, float fk, float vf, int &e0,
+                                        float (&Fv)[4]) {
+    const float gk = fmaf(C.sv, fk, T.g0);
+    const float cN = fmaf(gk, T.eN, vf), cF = fmaf(gk, T.eF, vf);
+    float t0 = cN - T.hN, t1 = cN + T.hN, t2 = cF - T.hF, t3 = cF + T.hF;
+    sort4(t0, t1, t2, t3);
+    const Trap Tv = nc_trap(t0, t1, t2, t3);
+    e0 = (int)floorf(Tv.k0 + 0.5f);
+    nc_cells<4>(Tv, e0, (int)floorf(Tv.k3 + 0.5f), Fv);
+}
+
+// the 4-cell window [as, as + 3] inside the detector (nu >= 4) for the weights
+// F of cells a0 .. a0 + 3: shifted when the footprint sits on the last cells
+__device__ __forceinline__ int window4(const float (&F)[4], int a0, int nu, float (&Fu)[4]) {
+    const int as = min(a0, nu - 4);
+    const int sh = a0 - as;  // 0..3
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float w = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) w = (q - sh == p) ? F[p] : w;
+        Fu[q] = w;
+    }
+    return as;
 }
 
 // Non-circular flat geometry: everything per voxel.
@@ -147,11 +206,14 @@ __device__ __forceinline__ float fp_amp(const C_ &C, float wz) {
 // normalised footprints as the interpolation (Sec. 2.3): the voxel's weight
 // is the depth weight rc_w / depth^2 over the footprint's transaxial area
 // (cells) and axial height (rows), constant down a column.
-template <typename TIn, bool CURVED, bool DD, int ZT, bool RECON = false>
+// TT: SF-TT (flat detector), on a sinogram already scaled by the per-cell
+// amplitude A2; its axial trapezoids reach further, so the row buffer holds
+// ZT + 6 rows.
+template <typename TIn, bool CURVED, bool DD, int ZT, bool RECON = false, bool TT = false>
 __global__ void __launch_bounds__(128, 7)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
-    constexpr int NR = ZT + 3;  // rows -1 .. ZT + 1 relative to the chunk's first voxel
+    constexpr int NR = TT ? ZT + 6 : ZT + 3;  // SF, DD: rows -1 .. ZT + 1 relative to the chunk's first voxel
     __shared__ CtView sview[kViews];
     __shared__ float Rs[NR][128];
     __shared__ float Gs[ZT][128];  // general-path partial sums (thread-private slots)
@@ -186,6 +248,87 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             d0 = max(d0, -C.aref);
             d1 = min(d1, g.nu - 1 - C.aref);
             if (d0 > d1) continue;
+            const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
+            if constexpr (TT) {
+                const TtCol T = tt_col(V, g, C, i, j);
+                if (d1 - d0 <= 3 && C.sv > 0.f && g.nu >= 4) {
+                    // every knot rises with k (slope sv (1 + e) > 0): the
+                    // chunk's rows run from the first voxel's lowest knot to
+                    // the last voxel's highest
+                    int bref0;
+                    float frac0;
+                    split_cell(fmaf(C.sv, (float)kbeg, C.fv0), bref0, frac0);
+                    const float gb = fmaf(C.sv, (float)kbeg, T.g0), ge = fmaf(C.sv, (float)(kend - 1), T.g0);
+                    const float relL = fmaf(C.sv, (float)(kend - 1 - kbeg), frac0);
+                    const float lo = fminf(fmaf(gb, T.eN, frac0) - T.hN, fmaf(gb, T.eF, frac0) - T.hF);
+                    const float hi = fmaxf(fmaf(ge, T.eN, relL) + T.hN, fmaf(ge, T.eF, relL) + T.hF);
+                    const int ef = (int)floorf(lo + 0.5f), el = (int)floorf(hi + 0.5f);
+                    if (el - ef + 4 <= NR) {
+                        float F[4], Fu[4];
+                        trap_cells4(C.T, d0, d1, F);
+                        const int as = window4(F, C.aref + d0, g.nu, Fu);
+                        // Rs[e - ef] = row bref0 + e filtered by Fu, for e in
+                        // [ef, el + 3] (zero off the detector)
+                        const int va = max(ef, -bref0), vb = min(el, g.nv - 1 - bref0);
+                        const TIn *ya = yv + as;
+                        for (int e = ef; e < min(va, el + 1); ++e) Rs[e - ef][tid] = 0.f;
+#pragma unroll 4
+                        for (int e = va; e <= vb; ++e) {
+                            const TIn *row = ya + (size_t)(bref0 + e) * g.nu;
+                            float R = Fu[0] * ld(row, 0);
+                            R = fmaf(Fu[1], ld(row, 1), R);
+                            R = fmaf(Fu[2], ld(row, 2), R);
+                            R = fmaf(Fu[3], ld(row, 3), R);
+                            Rs[e - ef][tid] = R;
+                        }
+                        for (int e = max(vb + 1, ef); e <= el + 3; ++e) Rs[e - ef][tid] = 0.f;
+#pragma unroll 1
+                        for (int kk = 0; kk < ZT; ++kk) {
+                            if (kbeg + kk >= kend) break;
+                            int e0;
+                            float Fv[4];
+                            tt_rows(C, T, (float)(kbeg + kk), fmaf(C.sv, (float)kk, frac0), e0, Fv);
+                            const int ix = min(max(e0 - ef, 0), NR - 4);
+                            float s = Fv[0] * Rs[ix][tid];
+                            s = fmaf(Fv[1], Rs[ix + 1][tid], s);
+                            s = fmaf(Fv[2], Rs[ix + 2][tid], s);
+                            s = fmaf(Fv[3], Rs[ix + 3][tid], s);
+                            Gs[kk][tid] += s;
+                        }
+                        continue;
+                    }
+                }
+                // general footprints: each voxel's rows read directly
+                for (int db = d0; db <= d1; db += 4) {
+                    float Fu[4];
+                    trap_cells4(C.T, db, d1, Fu);
+                    const int abase = C.aref + db;
+                    const int na = min(4, d1 - db + 1);
+#pragma unroll 1
+                    for (int kk = 0; kk < ZT; ++kk) {
+                        const int k = kbeg + kk;
+                        if (k >= kend) break;
+                        int bref, e0;
+                        float vf, Fv[4];
+                        split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+                        tt_rows(C, T, (float)k, vf, e0, Fv);
+                        float s = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int b = bref + e0 + q;
+                            if (b < 0 || b >= g.nv) continue;
+                            const TIn *row = yv + (size_t)b * g.nu + abase;
+                            float r = Fu[0] * ld(row, 0);
+                            if (na > 1) r = fmaf(Fu[1], ld(row, 1), r);
+                            if (na > 2) r = fmaf(Fu[2], ld(row, 2), r);
+                            if (na > 3) r = fmaf(Fu[3], ld(row, 3), r);
+                            s = fmaf(Fv[q], r, s);
+                        }
+                        Gs[kk][tid] += s;
+                    }
+                }
+                continue;
+            }
             float rw = 0.f;
             if (RECON) {
                 const float fi = (float)i, fj = (float)j;
@@ -195,23 +338,10 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                 const float area = 0.5f * ((C.T.k3 - C.T.k0) + (C.T.k2 - C.T.k1));
                 rw = V.rc_w / (den2 * area * (2.f * C.hv));
             }
-            const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
             if (d1 - d0 <= 3 && C.hv < 0.5f && C.sv > 0.f && g.nu >= 4) {
-                float F[4];
+                float F[4], Fu[4];
                 trap_cells4(C.T, d0, d1, F);
-                // 4-cell window [as, as + 3] inside the detector; shift the
-                // weights when the footprint sits on the last cells
-                const int a0 = C.aref + d0;
-                const int as = min(a0, g.nu - 4);
-                const int sh = a0 - as;  // 0..3
-                float Fu[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float w = 0.f;
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) w = (q - sh == p) ? F[p] : w;
-                    Fu[q] = w;
-                }
+                const int as = window4(F, C.aref + d0, g.nu, Fu);
                 // Rows relative to the chunk's first voxel: voxel kk sits at
                 // rel = frac0 + sv kk rows from row bref0 (0 < sv < 1), so it
                 // touches rows e0, e0 + 1 with e0 in [-1, ZT - 1].
@@ -222,7 +352,7 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                 const int ef = (int)floorf(frac0 - C.hv + 0.5f), el = (int)floorf(last + C.hv + 0.5f);
                 const int va = max(ef, -bref0), vb = min(el, g.nv - 1 - bref0);  // rows on the detector
                 const TIn *ya = yv + as;
-                for (int e = ef; e < va; ++e) Rs[e + 1][tid] = 0.f;
+                for (int e = ef; e < min(va, el + 1); ++e) Rs[e + 1][tid] = 0.f;  // a chunk below the detector zeroes [ef, el] only
 #pragma unroll 4
                 for (int e = va; e <= vb; ++e) {
                     const TIn *row = ya + (size_t)(bref0 + e) * g.nu;
@@ -414,9 +544,55 @@ __device__ __forceinline__ void vx_stage1(const CtView &V, const CtGrid &g, int 
     }
 }
 
-// (with up to 4 cells per item the kernel fits 80 registers: 3 blocks per SM)
-template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false>
-__global__ void __launch_bounds__(256, NA <= 4 ? 3 : 2)
+// SF-TT stage 1 of the streaming forward (flat detector): the column's
+// SF-TR transaxial weights are in Fu already; each voxel spreads x over the
+// rows of its axial trapezoid (amplitude 1: A2 is applied per cell).
+template <typename TIn, int BV>
+__device__ __forceinline__ void tt_stage1(const CtView &V, const CtGrid &g, const SfCol &C, int i, int j, int B0,
+                                          int bt, const TIn *__restrict__ x, const TIn *__restrict__ volZ,
+                                          float (&Z)[BV][kItems], int tid) {
+    const TtCol T = tt_col(V, g, C, i, j);
+    // voxels with a knot within a row of the tile (knots lie within the
+    // view's bound m_tt_v of the centre's projection)
+    const float hw = 0.5f + V.m_tt_v + kSearchPad;
+    const float rsv = 1.f / C.sv;
+    const float ka = ((float)B0 - C.fv0 - hw) * rsv;
+    const float kb = ((float)(B0 + BV - 1) - C.fv0 + hw) * rsv;
+    const int k0 = max(0, (int)ceilf(fminf(ka, kb)));
+    const int k1 = min(g.nz - 1, (int)floorf(fmaxf(ka, kb)));
+    auto tap = [&](int k, float xv) {
+        int bref, e0;
+        float vf, Fv[4];
+        split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
+        tt_rows(C, T, (float)k, vf, e0, Fv);
+        const int r0 = bref + e0 - B0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (r0 + q >= 0 && r0 + q < BV) Z[r0 + q][tid] = fmaf(Fv[q], xv, Z[r0 + q][tid]);
+    };
+    if (volZ != nullptr) {  // contiguous column of the z-major copy, 4 voxels per load
+        const TIn *cz = volZ + (size_t)bt * g.nx * g.ny * g.nz + ((size_t)j * g.nx + i) * g.nz;
+#pragma unroll 1
+        for (int kq = k0 & ~3; kq <= k1; kq += 4) {
+            float xv[4];
+            ld4(cz + kq, xv);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (kq + t >= k0 && kq + t <= k1) tap(kq + t, xv[t]);
+        }
+    } else {
+        const TIn *xc = x + (size_t)j * g.nx + i;
+        const size_t zs = (size_t)g.nx * g.ny;
+#pragma unroll 1
+        for (int k = k0; k <= k1; ++k) tap(k, ld(xc, (size_t)k * zs));
+    }
+}
+
+// (with up to 4 cells per item the SF-TR, DD and voxel-driven kernels fit 80
+// registers: 3 blocks per SM)
+// TT: SF-TT (flat detector); the per-cell amplitude A2 is applied after the gather.
+template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false, bool TT = false>
+__global__ void __launch_bounds__(256, (NA <= 4 && !TT) ? 3 : 2)
 sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol,
             const TIn *__restrict__ volZ, void *__restrict__ sino, int out_t, int tiles_u, int tiles_v) {
     constexpr int BV = 8 * RPT;
@@ -435,7 +611,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
     const SlabCoef sc = slab_coef(V, main_y);
     // search half widths: footprint bound + half a cell, or the hat's one cell
     const float mu = VOX ? 1.f + kSearchPad : (DD ? V.m_dd_u : V.m_sf_u) + 0.5f + kSearchPad;
-    const float mv = VOX ? 1.f + kSearchPad : V.m_sf_v + 0.5f + kSearchPad;
+    const float mv = VOX ? 1.f + kSearchPad : (TT ? V.m_tt_v : V.m_sf_v) + 0.5f + kSearchPad;
     const int nslab = main_y ? g.ny : g.nx, nlat = main_y ? g.nx : g.ny;
     const TIn *x = vol + (size_t)bt * g.nx * g.ny * g.nz;
     const float T1 = Det<CURVED>::ratio_at(V, a - mu), T2 = Det<CURVED>::ratio_at(V, a + mu);
@@ -487,6 +663,9 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 S.a0[tid] = C.aref + d0;
 #pragma unroll
                 for (int r = 0; r < BV; ++r) S.Z[r][tid] = 0.f;
+                if constexpr (TT) {
+                    tt_stage1<TIn, BV>(V, g, C, i, j, B0, bt, x, volZ, S.Z, tid);
+                } else {
                 // voxels whose axial rectangle can meet a row of the tile
                 const float hw = 0.5f + C.hv + kSearchPad;
                 const float rsv = 1.f / C.sv;
@@ -553,6 +732,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                     }
                 }
                 }
+                }
             }
             __syncthreads();
             // ---- stage 2: thread = (cell a, rows B0 + threadIdx.y + 8 r)
@@ -591,7 +771,8 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
             const int b = B0 + threadIdx.y + 8 * r;
             if (b < g.nv)
                 st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + a,
-                   DD ? acc[r] * dd_len<CURVED>(V, g, a, b) : acc[r], out_t);
+                       DD ? acc[r] * dd_len<CURVED>(V, g, a, b) : (TT ? acc[r] * tt_amp(V, g, a, b) : acc[r]),
+                       out_t);
         }
     }
 }
@@ -762,12 +943,12 @@ to_zmajor(const T *__restrict__ x, T *__restrict__ xZ, int nx, int ny, int nz) {
 namespace {
 constexpr int kZT = 16;
 
-template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false>
+template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false, bool TT = false>
 cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                           int batch, cudaStream_t st) {
     const int tiles_u = (g.nu + 31) / 32, tiles_v = (g.nv + 8 * RPT - 1) / (8 * RPT);
     const size_t smem = sizeof(SfFwdSmem<RPT, NA>);
-    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT, NA, VOX>,
+    cudaError_t e = cudaFuncSetAttribute(sf_fwd_circ<TIn, CURVED, DD, RPT, NA, VOX, TT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a z-major copy of the volume (pooled workspace) makes every column walk
@@ -785,8 +966,8 @@ cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, 
         }
     }
     dim3 blk(32, 8), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
-    sf_fwd_circ<TIn, CURVED, DD, RPT, NA, VOX><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u,
-                                                                  tiles_v);
+    sf_fwd_circ<TIn, CURVED, DD, RPT, NA, VOX, TT><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u,
+                                                                      tiles_v);
     e = cudaGetLastError();
     if (xZ) {
         const cudaError_t ef = workspace_free(xZ, st);
@@ -816,12 +997,12 @@ cudaError_t fp_fwd_circ(const CtGrid &g, const CtView *views, const TIn *src, vo
     return cudaGetLastError();
 }
 
-template <typename TIn, bool CURVED, bool DD, bool RECON = false>
+template <typename TIn, bool CURVED, bool DD, bool RECON = false, bool TT = false>
 cudaError_t fp_back_circ(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                          int batch, cudaStream_t st) {
     const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
     dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-    sf_back_circ<TIn, CURVED, DD, kZT, RECON><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    sf_back_circ<TIn, CURVED, DD, kZT, RECON, TT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     return cudaGetLastError();
 }
 
@@ -977,6 +1158,35 @@ cudaError_t launch_vx_fwd_circ(const CtGrid &g, const CtView *views, int in_t, c
     case 0: return vx_fwd_t<float>(g, views, in, out, out_t, batch, st);
     case 1: return vx_fwd_t<__half>(g, views, in, out, out_t, batch, st);
     default: return vx_fwd_t<__nv_bfloat16>(g, views, in, out, out_t, batch, st);
+    }
+}
+
+namespace {
+template <typename TIn>
+cudaError_t sftt_circ_fwd_t(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
+                            cudaStream_t st) {
+    const TIn *src = static_cast<const TIn *>(in);
+    if (g.max_m_sf_u <= 1.5f) {
+        if (g.nv >= 64) return fp_fwd_stream<TIn, false, false, 8, 4, false, true>(g, views, src, out, out_t, batch, st);
+        return fp_fwd_stream<TIn, false, false, 1, 4, false, true>(g, views, src, out, out_t, batch, st);
+    }
+    if (g.nv >= 64) return fp_fwd_stream<TIn, false, false, 8, 8, false, true>(g, views, src, out, out_t, batch, st);
+    return fp_fwd_stream<TIn, false, false, 1, 8, false, true>(g, views, src, out, out_t, batch, st);
+}
+}  // namespace
+
+bool sftt_circ_fits(const CtGrid &g) {
+    return g.variant == GEO_CIRC_FLAT && !g.is2d && g.max_m_sf_u <= 3.5f && g.max_m_tt_v <= 1.5f;
+}
+
+cudaError_t launch_sftt_circ(int dir, const CtGrid &g, const CtView *views, int in_t, const void *in, int out_t,
+                             void *out, int batch, cudaStream_t st) {
+    if (dir == 1) return fp_back_circ<float, false, false, false, true>(g, views, static_cast<const float *>(in),
+                                                                        out, out_t, batch, st);
+    switch (in_t) {
+    case 0: return sftt_circ_fwd_t<float>(g, views, in, out, out_t, batch, st);
+    case 1: return sftt_circ_fwd_t<__half>(g, views, in, out, out_t, batch, st);
+    default: return sftt_circ_fwd_t<__nv_bfloat16>(g, views, in, out, out_t, batch, st);
     }
 }
 

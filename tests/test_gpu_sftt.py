@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 
 import oracle
 import workloads as W
-from gpu_util import TOL_F32, ragged, rel_l2
+from gpu_util import TOL_F16, TOL_F32, ragged, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -86,3 +86,50 @@ def test_sftt_refuses_what_it_does_not_provide(ct):
     gw = ct.Geometry.from_spec(wide)
     with pytest.raises(ct.CTError):
         ct.forward(gw, torch.rand(gw.vol_shape, device="cuda"), "sftt")
+
+
+# circular flat 3D geometry runs the column-walk kernels (transaxial footprint
+# once per column and view): the ragged case (strided column reads, one-row
+# tiles, voxels taller than a row) plus these regimes
+CIRC_REGIMES = {
+    # z-major column copy (nz a multiple of 4), 64-row tiles, voxels shorter than a row
+    "zmajor": dict(nz=24, nv=70, dz=0.8),
+    # transaxial footprints of 5..8 cells
+    "cells8": dict(nu=150, du=0.9),
+    # axial trapezoids of up to 4 rows, two 64-row tiles
+    "rows4": dict(nv=70, dv=1.4),
+    # voxels shorter than a row with 64-row tiles and strided column reads
+    "short": dict(nz=37, nv=66, dz=0.7),
+}
+
+
+@pytest.mark.parametrize("regime", sorted(CIRC_REGIMES))
+def test_sftt_circular_regimes(ct, regime):
+    spec = dataclasses.replace(ragged("circ3d", "flat", seed=64), **CIRC_REGIMES[regime])
+    g = ct.Geometry.from_spec(spec)
+    x = W.phantom(spec, seed=5)
+    ref = oracle.forward(spec, "sftt", x)
+    y = ct.forward(g, torch.as_tensor(x, dtype=torch.float32).cuda(), "sftt")
+    assert rel_l2(y.cpu().numpy(), ref) <= TOL_F32
+    s = W.random_sino(spec, seed=6)[0]
+    refb = oracle.back(spec, "sftt", s)
+    xb = ct.back(g, torch.as_tensor(s, dtype=torch.float32).cuda(), "sftt")
+    assert rel_l2(xb.cpu().numpy(), refb) <= TOL_F32
+
+
+def test_sftt_circular_adjoint_batches_and_half(ct):
+    spec = dataclasses.replace(ragged("circ3d", "flat", seed=66), nz=24, nv=70, dz=0.8)
+    g = ct.Geometry.from_spec(spec)
+    gen = torch.Generator(device="cuda").manual_seed(8)
+    x = torch.rand((2,) + spec.vol_shape, generator=gen, device="cuda")
+    y = torch.rand((2,) + spec.sino_shape, generator=gen, device="cuda")
+    Ax, Aty = ct.forward(g, x, "sftt"), ct.back(g, y, "sftt")
+    lhs, rhs = float((Ax.double() * y.double()).sum()), float((x.double() * Aty.double()).sum())
+    assert abs(lhs - rhs) <= TOL_F32 * abs(lhs)
+    assert torch.equal(Ax[1], ct.forward(g, x[1].contiguous(), "sftt"))
+    assert torch.equal(Aty[0], ct.back(g, y[0].contiguous(), "sftt"))
+    # FP16 storage: FP32 arithmetic on the rounded input, one rounding at the store
+    xh = x[0].half()
+    ref = oracle.forward(spec, "sftt", xh.float().cpu().numpy().astype(np.float64))
+    yh = ct.forward(g, xh, "sftt", out_dtype=torch.float16)
+    assert rel_l2(yh.float().cpu().numpy(), ref) <= TOL_F16
