@@ -147,3 +147,18 @@ def test_fbp_batches_are_independent(ct):
     for proj in ("dd", "sf"):
         xb = ct.back(g, q, proj, mode="recon")
         assert torch.equal(xb[1, 2], ct.back(g, q[1, 2].contiguous(), proj, mode="recon"))
+
+
+@pytest.mark.parametrize("det", ["flat", "curved"])
+@pytest.mark.parametrize("nu", [1000, 4097, 16384])
+def test_ramp_filter_wide_rows(ct, det, nu):
+    """Rows far wider than one thread block's outputs, up to the widest row the
+    filter takes (16384 cells: its shared-memory row and taps nearly fill a
+    block's 227 KB), even and odd widths."""
+    spec = W.GeometrySpec("circ3d", det, 16, 16, 4, 1.0, 1.0, 1.0, nu, 3, 16.0 * 40 / nu, 1.0, 3,
+                          theta=np.array([0.0, 2.0, 4.0]), sad=300.0, sdd=600.0, u_ofst=1.3, v_ofst=0.4)
+    y = W.random_sino(spec, seed=9)[0]
+    ref = oracle.ramp_filter(spec, y)
+    g = ct.Geometry.from_spec(spec)
+    q = ct.ramp_filter(g, torch.as_tensor(y, dtype=torch.float32).cuda())
+    assert rel_l2(q.cpu().numpy(), ref) <= TOL_F32
