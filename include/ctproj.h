@@ -171,8 +171,10 @@ ct_status ct_forward(const ct_geometry *geom, ct_projector proj, ct_mode mode,
  * sino: device pointer, batch x nview x nv x nu elements of type in_t.
  * vol:  device pointer, batch x nz x ny x nx elements of type out_t;
  *       overwritten.  Other arguments as for ct_forward.
- * CT_DD and CT_SF_TT use the pooled stream-ordered workspace of the
- * threading note above; CT_ERR_OOM when it cannot be had. */
+ * CT_DD, CT_SF_TT and CT_RAY in circular geometry (its sinogram scaled by
+ * each cell ray's secant against its horizontal path) use the pooled
+ * stream-ordered workspace of the threading note above; CT_ERR_OOM when it
+ * cannot be had. */
 ct_status ct_back(const ct_geometry *geom, ct_projector proj, ct_mode mode,
                   ct_dtype in_t, const void *sino, ct_dtype out_t, void *vol,
                   int batch, void *cuda_stream);

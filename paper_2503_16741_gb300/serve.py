@@ -66,7 +66,10 @@ def shapes(geom: Dict[str, Any]):
 
 def request_bytes(req: Request) -> int:
     """Device bytes a request holds while it runs: input, output and, for
-    MBIR and FBP, the residual or filtered sinogram (FP32 for FBP)."""
+    MBIR and FBP, the residual or filtered sinogram (FP32 for FBP).  The
+    library's own scratch (the z-major volume copy of the forwards, the
+    scaled FP32 sinogram of the DD, SF-TT and circular ray-driven backs)
+    comes from its stream-ordered pool and is not counted here."""
     vol, sino = shapes(req.geometry)
     nv, ns = int(np.prod(vol)), int(np.prod(sino))
     it = ITEMSIZE[req.dtype]

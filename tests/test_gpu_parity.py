@@ -194,3 +194,24 @@ def test_long_object_beyond_the_detector(ct, det):
     for proj in ("voxel", "dd", "sf"):
         ref = oracle.back_recon(spec, q, proj)
         assert rel_l2(ct.back(g, qt, proj, mode="recon").cpu().numpy(), ref) <= TOL_F32, proj
+
+
+@pytest.mark.parametrize("det", ["flat", "curved"])
+def test_ray_back_narrow_shadows(ct, det):
+    """Cells wider than a voxel's shadow (footprint bound below one cell): the
+    circular ray back takes its two-cell groups; forward and back against the
+    oracle, and the adjoint identity."""
+    import dataclasses
+    spec = dataclasses.replace(ragged("circ3d", det, seed=67), nu=42, du=3.2)
+    g = _gpu(ct, spec)
+    x = W.phantom(spec, seed=3)
+    s = W.random_sino(spec, seed=4)[0]
+    xt = torch.as_tensor(x, dtype=torch.float32).cuda()
+    st = torch.as_tensor(s, dtype=torch.float32).cuda()
+    y = ct.forward(g, xt, "ray")
+    assert rel_l2(y.cpu().numpy(), oracle.forward(spec, "ray", x)) <= TOL_F32
+    xb = ct.back(g, st, "ray")
+    assert rel_l2(xb.cpu().numpy(), oracle.back(spec, "ray", s)) <= TOL_F32
+    lhs = float((y.double() * st.double()).sum())
+    rhs = float((xt.double() * xb.double()).sum())
+    assert abs(lhs - rhs) <= TOL_F32 * abs(lhs)
