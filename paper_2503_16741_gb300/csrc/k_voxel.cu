@@ -66,10 +66,17 @@ __device__ __forceinline__ float bilinear(const TIn *yv, const CtGrid &g, float 
 // 2.3): the same bilinear interpolation with the depth weight in place of the
 // voxel-driven amplitude, rc_w / depth^2 (flat: dbeta R D / ((X-s).n)^2;
 // curved: dbeta / rho^2), constant down a column in circular geometry.
+// Circular geometry: a column's two cells and their hat weights hold for all
+// its voxels, so each detector row the chunk reaches is filtered once along u
+// into a thread-private slice of shared memory, and each voxel blends its two
+// rows (the same operations, in the same order, as the per-voxel bilinear);
+// chunks whose rows do not fit the slice take the per-voxel form.
 template <typename TIn, bool CURVED, int ZT, bool RECON = false>
 __global__ void __launch_bounds__(128)
 vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
+    constexpr int NR = ZT + 1;  // rows floor(fv) - B .. + 1 of the chunk's voxels, B the first voxel's row
+    __shared__ float Rs[NR][128];
     int bx = blockIdx.x;
     const int tx = bx % tiles_x; bx /= tiles_x;
     const int kc = bx % nzc;
@@ -77,7 +84,9 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
     const int i = tx * 32 + threadIdx.x;
     const int j = blockIdx.y * 4 + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const int kbeg = kc * ZT;
+    const int kend = min(kbeg + ZT, g.nz);
     float acc[ZT];
 #pragma unroll
     for (int q = 0; q < ZT; ++q) acc[q] = 0.f;
@@ -89,6 +98,38 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
         if (C.fu <= -1.f || C.fu >= (float)g.nu) continue;
         const TIn *yv = ys + (size_t)v * vstride;
         const float wr = RECON ? V.rc_w / (C.den * C.den) : 0.f;
+        // rows of the chunk: fv rises with k (sv > 0)
+        const float Bf = floorf(fmaf(C.sv, (float)kbeg, C.fv0));
+        const int B = (int)Bf;
+        const int eL = (int)floorf(fmaf(C.sv, (float)(kend - 1), C.fv0)) - B + 1;
+        if (C.sv > 0.f && eL < NR) {
+            const float a0f = floorf(C.fu);
+            const int a0 = (int)a0f;
+            const float ta = C.fu - a0f;
+            const bool in0 = a0 >= 0 && a0 < g.nu, in1 = a0 + 1 >= 0 && a0 + 1 < g.nu;
+            for (int e = 0; e <= eL; ++e) {
+                const int b = B + e;
+                float r = 0.f;
+                if (b >= 0 && b < g.nv) {
+                    const TIn *row = yv + (size_t)b * g.nu;
+                    if (in0) r = (1.f - ta) * ld(row, (size_t)a0);
+                    if (in1) r = fmaf(ta, ld(row, (size_t)(a0 + 1)), r);
+                }
+                Rs[e][tid] = r;
+            }
+#pragma unroll
+            for (int kk = 0; kk < ZT; ++kk) {
+                const int k = kbeg + kk;
+                if (k >= kend) break;
+                const float fv = fmaf(C.sv, (float)k, C.fv0);
+                const float bf = floorf(fv);
+                const float tb = fv - bf;
+                const int e0 = min(max((int)bf - B, 0), NR - 2);
+                const float sb = fmaf(tb, Rs[e0 + 1][tid], (1.f - tb) * Rs[e0][tid]);
+                acc[kk] = fmaf(RECON ? wr : vx_amp_col(C, g, V, k), sb, acc[kk]);
+            }
+            continue;
+        }
 #pragma unroll
         for (int kk = 0; kk < ZT; ++kk) {
             const int k = kbeg + kk;
@@ -181,7 +222,8 @@ vx_fwd_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vo
 
 // ------------------------------------------------------------ launchers
 namespace {
-constexpr int kZT = 8;
+constexpr int kZT = 8;    // voxels per thread, non-circular back
+constexpr int kZTc = 16;  // circular back
 
 template <typename TIn>
 cudaError_t vx_launch_t(int dir, const CtGrid &g, const CtView *views, const void *in, void *out,
@@ -192,14 +234,16 @@ cudaError_t vx_launch_t(int dir, const CtGrid &g, const CtView *views, const voi
         dim3 blk(32, 8), grd((unsigned)(tiles_u * g.nview * batch), (unsigned)((g.nv + 7) / 8));
         vx_fwd_nc<TIn><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_u);
     } else {
-        const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+        const int tiles_x = (g.nx + 31) / 32;
+        const int nzc = (g.nz + kZT - 1) / kZT, nzcc = (g.nz + kZTc - 1) / kZTc;
         dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+        dim3 grdc((unsigned)(tiles_x * nzcc * batch), (unsigned)((g.ny + 3) / 4));
         if (g.variant == GEO_NONCIRC_FLAT)
             vx_back_nc<TIn, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
         else if (g.variant == GEO_CIRC_CURVED)
-            vx_back_circ<TIn, true, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+            vx_back_circ<TIn, true, kZTc><<<grdc, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzcc);
         else
-            vx_back_circ<TIn, false, kZT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+            vx_back_circ<TIn, false, kZTc><<<grdc, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzcc);
     }
     return cudaGetLastError();
 }
@@ -210,14 +254,16 @@ template <typename TIn>
 cudaError_t vx_recon_t(const CtGrid &g, const CtView *views, const void *in, void *out, int out_t, int batch,
                        cudaStream_t st) {
     const TIn *src = static_cast<const TIn *>(in);
-    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+    const int tiles_x = (g.nx + 31) / 32;
+    const int nzc = (g.nz + kZT - 1) / kZT, nzcc = (g.nz + kZTc - 1) / kZTc;
     dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
+    dim3 grdc((unsigned)(tiles_x * nzcc * batch), (unsigned)((g.ny + 3) / 4));
     if (g.variant == GEO_NONCIRC_FLAT)
         vx_back_nc<TIn, kZT, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     else if (g.variant == GEO_CIRC_CURVED)
-        vx_back_circ<TIn, true, kZT, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        vx_back_circ<TIn, true, kZTc, true><<<grdc, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzcc);
     else
-        vx_back_circ<TIn, false, kZT, true><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+        vx_back_circ<TIn, false, kZTc, true><<<grdc, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzcc);
     return cudaGetLastError();
 }
 }  // namespace

@@ -28,7 +28,7 @@ def _sample_voxels(spec, n, seed):
     return rng.choice(spec.n_vox, size=n, replace=False)
 
 
-@pytest.mark.parametrize("proj", ["sf", "dd", "ray"])
+@pytest.mark.parametrize("proj", ["sf", "dd", "ray", "voxel"])
 def test_circ3d_256_full_size(ct, proj):
     spec = W.circ3d_256()
     x = W.phantom(spec, seed=0)
