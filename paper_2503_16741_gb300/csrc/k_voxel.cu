@@ -106,16 +106,17 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             const float a0f = floorf(C.fu);
             const int a0 = (int)a0f;
             const float ta = C.fu - a0f;
-            const bool in0 = a0 >= 0 && a0 < g.nu, in1 = a0 + 1 >= 0 && a0 + 1 < g.nu;
+            // cells and rows off the detector weigh zero; their loads read a
+            // clamped in-range address, so the loads carry no branches
+            const float w0 = (a0 >= 0 && a0 < g.nu) ? 1.f - ta : 0.f;
+            const float w1 = (a0 + 1 >= 0 && a0 + 1 < g.nu) ? ta : 0.f;
+            const int ac0 = min(max(a0, 0), g.nu - 1), ac1 = min(max(a0 + 1, 0), g.nu - 1);
+#pragma unroll 4
             for (int e = 0; e <= eL; ++e) {
                 const int b = B + e;
-                float r = 0.f;
-                if (b >= 0 && b < g.nv) {
-                    const TIn *row = yv + (size_t)b * g.nu;
-                    if (in0) r = (1.f - ta) * ld(row, (size_t)a0);
-                    if (in1) r = fmaf(ta, ld(row, (size_t)(a0 + 1)), r);
-                }
-                Rs[e][tid] = r;
+                const TIn *row = yv + (size_t)min(max(b, 0), g.nv - 1) * g.nu;
+                const float r = fmaf(w1, ld(row, (size_t)ac1), w0 * ld(row, (size_t)ac0));
+                Rs[e][tid] = (b >= 0 && b < g.nv) ? r : 0.f;
             }
 #pragma unroll
             for (int kk = 0; kk < ZT; ++kk) {
