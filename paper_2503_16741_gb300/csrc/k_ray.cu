@@ -136,34 +136,19 @@ __device__ __forceinline__ float chord(const float e[3], const float dh[3], cons
     return fmaxf(hi - lo, 0.f);
 }
 
-// offset, at the voxel's depth, of the central ray of cell (a, b) from the
+// flat detector (the non-circular back): chord of cell (a, b)'s central ray
+// through the voxel, from the ray's offset at the voxel's depth cn to the
 // voxel centre, formed from the cell-relative positions (a - fu), (b - fv)
-template <bool CURVED>
-__device__ __forceinline__ float ray_weight(const CtView &V, const CtGrid &g, int a, int b, float dfu,
-                                            float dfv, float cn, float rho, const float hh[3]) {
+__device__ __forceinline__ float ray_weight_flat(const CtView &V, const CtGrid &g, int a, int b, float dfu,
+                                                 float dfv, float cn, const float hh[3]) {
     float d[3], e[3];
-    ray_dir<CURVED>(V, g, a, b, d);
+    ray_dir<false>(V, g, a, b, d);
     const float il = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
-    float dh[3] = {d[0] * il, d[1] * il, d[2] * il};
-    if (CURVED) {
-        // dfu = a - fu (cells): angle of the voxel centre from the ray plane
-        const float dg = -dfu / V.Ku;
-        float sg, cg;
-        sincosf(((float)a - V.Cu) / V.Ku, &sg, &cg);
-        float sd, cd;
-        sincosf(dg, &sd, &cd);
-        const float s2 = sinf(0.5f * dg);
-        const float lat = -rho * sd;  // along m_perp = cos(ga) e_u - sin(ga) n
-        const float vert = (rho / V.D) * g.dv * (dfv - 2.f * s2 * s2 * ((float)b - V.Cv));
+    const float dh[3] = {d[0] * il, d[1] * il, d[2] * il};
+    const float sc = cn / V.D;
+    const float eu = sc * g.du * dfu, ev = sc * g.dv * dfv;
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-            e[m] = fmaf(lat, fmaf(cg, V.eu[m], -sg * V.nn[m]), vert * V.ev[m]);
-    } else {
-        const float sc = cn / V.D;
-        const float eu = sc * g.du * dfu, ev = sc * g.dv * dfv;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) e[m] = fmaf(eu, V.eu[m], ev * V.ev[m]);
-    }
+    for (int m = 0; m < 3; ++m) e[m] = fmaf(eu, V.eu[m], ev * V.ev[m]);
     return chord(e, dh, hh);
 }
 
@@ -432,7 +417,7 @@ ray_back_nc(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                 const TIn *row = yv + (size_t)b * g.nu;
                 for (int d = d0; d <= d1; ++d) {
                     const int a = aref + d;
-                    const float w = ray_weight<false>(V, g, a, b, (float)d - fr, (float)e - vr, cn, cn, hh);
+                    const float w = ray_weight_flat(V, g, a, b, (float)d - fr, (float)e - vr, cn, hh);
                     if (w > 0.f) s = fmaf(w, ld(row, (size_t)a), s);
                 }
             }
