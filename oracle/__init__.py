@@ -10,9 +10,13 @@ independent outer loops), built on first use with the system C compiler.
 Parity status per projector (what pins it in tests/test_oracle_*.py):
   ray-driven   brute-force all-pairs chord lengths, closed-form chords
   voxel-driven bilinear partition of unity, hand-derived single-voxel value
-  DD           boundary partition, parallel-beam equality with exact row sums
-  SF           trapezoid area identity, exact parallel-beam pixel projection
-and for all four the adjoint identity <Ax, y> = <x, A^T y>.
+  DD           boundary partition, parallel-beam equality with exact row sums,
+               3D partition with slab-method path lengths
+  SF           trapezoid area identity, exact parallel-beam pixel projection,
+               3D mass identity with the slab-method column chord
+  SF-TT        trapezoid areas with the slab-method per-cell amplitude
+hand-derived cone-beam weights off the mid-plane (SF, DD, SF-TT; flat and
+curved), and for all the adjoint identity <Ax, y> = <x, A^T y>.
 """
 from __future__ import annotations
 

@@ -4,12 +4,15 @@ with the amplitude of each cell divided out, a voxel's weights sum to the
 product of its two trapezoid areas -- the transaxial one from the four
 column corners, the axial one from the z faces at the corners nearest to
 and farthest from the source -- recomputed here from the pinned detector
-mapping, not from the footprint code."""
+mapping, not from the footprint code; A2 itself is measured as a chord by the
+slab method.  Hand-derived SF-TT weights off the mid-plane are pinned in
+test_oracle_cone_weights.py."""
 import numpy as np
 import pytest
 
 import oracle
 import workloads as W
+from brute import seg_lengths
 
 
 def _expected(spec, view, i, j, k):
@@ -43,9 +46,17 @@ def _expected(spec, view, i, j, k):
 
 
 def _a2(spec, f, view, a, b):
+    """A2 measured, not recomputed: the 3D chord of the ray from the source
+    to the cell centre through a square column of side dx centred on that
+    ray (Long et al.'s amplitude taken along the cell's ray), found by the
+    brute-force slab method."""
+    s = np.asarray(f["s"])
     C = oracle.cell_point(spec, view, int(a), int(b))
-    d = C - f["s"]
-    return spec.dx * np.linalg.norm(d) / max(abs(d[0]), abs(d[1]))
+    M = 0.5 * (s + C)
+    h = 0.5 * spec.dx
+    lo = np.array([[M[0] - h, M[1] - h, -1.0e6]])
+    hi = np.array([[M[0] + h, M[1] + h, 1.0e6]])
+    return float(seg_lengths(s, s + 4.0 * (C - s), lo, hi)[0])
 
 
 CASES = [
