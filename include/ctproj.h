@@ -207,10 +207,10 @@ ct_status ct_back_acc(const ct_geometry *geom, ct_projector proj, ct_mode mode,
  * by each cell's path length; here that scratch is a fixed device array of
  * 16,777,216 floats (64 MiB) compiled into the library, which every GPU that
  * loads the library holds until the process exits.
- *   geom:  a fan-beam or circular geometry (non-circular DD backprojection
- *          needs no scratch: use ct_back; CT_ERR_UNSUPPORTED here);
+ *   geom:  any geometry kind (fan-beam, circular, non-circular);
  *   sino, vol, in_t, out_t, batch, cuda_stream: as for ct_back; the caller
- *          owns both buffers.
+ *          owns both buffers, which must be device memory on the geometry's
+ *          device (a host pointer is CT_ERR_INVALID_ARG, as in ct_back).
  * Limit: batch x nview x nv x nu <= 16,777,216, else CT_ERR_INVALID_ARG.
  * The first call on a device looks up the array's device address once (with
  * that device current); make that first call before any stream capture.

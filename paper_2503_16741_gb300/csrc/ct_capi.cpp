@@ -129,6 +129,22 @@ std::vector<double> recon_dbetas(const ct_geometry_desc *d, const Param P[]) {
 
 void ctp::set_last_error(const std::string &msg) { g_err = msg; }
 
+namespace ctp {
+// Host-side check that p is device (or managed) memory: a host or unknown
+// pointer is rejected with CT_ERR_INVALID_ARG before any kernel is launched.
+ct_status check_device_ptr(const void *p, const char *what) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CT_ERR_INVALID_ARG, std::string(what) + ": not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(CT_ERR_INVALID_ARG, std::string(what) + ": not device memory");
+    return CT_OK;
+}
+}  // namespace ctp
+
 extern "C" {
 
 const char *ct_last_error(void) { return g_err.c_str(); }
@@ -346,17 +362,7 @@ ct_status ct_geometry_shape(const ct_geometry *g, int *nx, int *ny, int *nz, int
     return CT_OK;
 }
 
-static ct_status check_ptr(const void *p, const char *what) {
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CT_ERR_INVALID_ARG, std::string(what) + ": not a CUDA pointer");
-    }
-    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
-        return fail(CT_ERR_INVALID_ARG, std::string(what) + ": not device memory");
-    return CT_OK;
-}
+static ct_status check_ptr(const void *p, const char *what) { return ctp::check_device_ptr(p, what); }
 
 static ct_status project(int dir, const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t,
                          const void *in, ct_dtype out_t, void *out, int batch, float alpha, float beta,

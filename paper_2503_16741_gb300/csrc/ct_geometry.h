@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/ctproj.h"
 #include "ct_types.h"
 
 struct ct_geometry {
@@ -20,4 +21,6 @@ struct ct_geometry {
 namespace ctp {
 // message returned by ct_last_error() on this thread
 void set_last_error(const std::string &msg);
+// CT_OK if p is device or managed memory, else CT_ERR_INVALID_ARG (message set)
+ct_status check_device_ptr(const void *p, const char *what);
 }  // namespace ctp

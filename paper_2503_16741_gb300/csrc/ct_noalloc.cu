@@ -5,7 +5,9 @@
 // must not risk an allocation (and the implicit synchronisation it may bring)
 // on a latency-critical path.  Its scratch -- the sinogram scaled by each
 // cell's path length -- lives in a fixed-size device array compiled into the
-// library instead of coming from cudaMalloc or a memory pool.
+// library instead of coming from cudaMalloc or a memory pool.  It serves
+// every geometry kind: non-circular footprints wider than the footprint
+// kernels' 8 cells x 4 rows take the general gather, which needs no scratch.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -50,8 +52,6 @@ cudaError_t scratch_address(int dev, float **out) {
 extern "C" ct_status ct_back_dd_noalloc(const ct_geometry *g, ct_dtype in_t, const void *sino, ct_dtype out_t,
                                         void *vol, int batch, void *cuda_stream) {
     if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");
-    if (g->grid.variant == ctp::GEO_NONCIRC_FLAT)
-        return fail(CT_ERR_UNSUPPORTED, "non-circular DD backprojection needs no scratch: use ct_back");
     if (in_t < CT_F32 || in_t > CT_BF16 || out_t < CT_F32 || out_t > CT_BF16)
         return fail(CT_ERR_INVALID_ARG, "unknown dtype");
     if (!sino || !vol) return fail(CT_ERR_INVALID_ARG, "null data pointer");
@@ -65,8 +65,13 @@ extern "C" ct_status ct_back_dd_noalloc(const ct_geometry *g, ct_dtype in_t, con
     if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
         return fail(CT_ERR_INVALID_ARG, "the geometry's device is not the current device");
     if (dev < 0 || dev >= kMaxDevices) return fail(CT_ERR_INVALID_ARG, "device index out of range");
-    if ((long long)((g->nx + 31) / 32) * ((g->nz + 15) / 16) * batch > 2147483647LL)
+    if ((long long)((g->nx + 31) / 32) * ((g->nz + 7) / 8) * batch > 2147483647LL)
         return fail(CT_ERR_INVALID_ARG, "batch too large for one launch");
+    // a host or foreign pointer is an argument error, caught before any launch
+    ct_status st = ctp::check_device_ptr(sino, "input");
+    if (st != CT_OK) return st;
+    st = ctp::check_device_ptr(vol, "output");
+    if (st != CT_OK) return st;
     float *scratch = nullptr;
     cudaError_t e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));

@@ -1075,12 +1075,28 @@ cudaError_t dd_nc_back(const CtGrid &g, const CtView *views, const void *in, voi
 }
 }  // namespace
 
-// DD backprojection in circular geometry into caller-provided scratch of at
-// least batch x nview x nv x nu floats (no allocation).
+// DD backprojection into caller-provided scratch of at least
+// batch x nview x nv x nu floats (no allocation).  Non-circular footprints
+// beyond the footprint kernels' 8 x 4 cells take the general gather, which
+// needs no scratch.
 cudaError_t launch_dd_back_scratch(const CtGrid &g, const CtView *views, int in_t, const void *in,
                                    int out_t, void *out, int batch, float *scratch, cudaStream_t st) {
     const size_t n = (size_t)g.nview * g.nv * g.nu * batch;
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152u * 64u);
+    if (g.variant == GEO_NONCIRC_FLAT) {
+        if (!nc_footprint_fits(g, 1)) return launch_dd_nc(1, g, views, in_t, in, out_t, out, batch, st);
+        switch (in_t) {
+        case 0: dd_prescale<float, false><<<blocks, 256, 0, st>>>(g, views, (const float *)in, scratch, batch); break;
+        case 1: dd_prescale<__half, false><<<blocks, 256, 0, st>>>(g, views, (const __half *)in, scratch, batch); break;
+        default:
+            dd_prescale<__nv_bfloat16, false><<<blocks, 256, 0, st>>>(g, views, (const __nv_bfloat16 *)in, scratch,
+                                                                     batch);
+            break;
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_nc(1, 1, g, views, 0, scratch, out_t, out, batch, st);
+    }
     const bool curved = g.variant == GEO_CIRC_CURVED;
     switch (in_t) {
     case 0:
