@@ -588,6 +588,55 @@ __device__ __forceinline__ void tt_stage1(const CtView &V, const CtGrid &g, cons
     }
 }
 
+// Axial sweep of one column in circular geometry (SF-TR or DD, axial
+// rectangle narrower than a row).  Voxel k covers rows [p_k - hv, p_k + hv]
+// with p_k = sv k + fv0 and sv = 2 hv, so consecutive rectangles abut: the
+// column's axial profile is a step function (value amp x on each voxel's
+// rectangle) and Z(row) is its integral over the row.  Walking k upward, a
+// voxel either lies inside the current row (adds w val, w = sv) or crosses
+// its upper edge once: the part below closes the row, whose sum is stored
+// once, and the rest opens the next.  d is the distance from the voxel's
+// lower edge to that row edge.  The walk runs over whole groups of four
+// voxels [k0 & ~3, k1 | 3] of the z-major column (nz a multiple of 4);
+// voxels outside [k0, k1] reach only rows outside the tile, whose sums are
+// dropped.  Rows the walk does not reach are zero.
+template <typename TIn, bool DD, int BV>
+__device__ __forceinline__ void sf_sweep(const SfCol &C, const CtGrid &g, const CtView &V,
+                                         const TIn *__restrict__ cz, int k0, int k1, int B0,
+                                         float (&Z)[BV][kItems], int tid) {
+    const int ks = k0 & ~3, ke = k1 | 3;
+    const float w = C.sv;
+    int bref;
+    float frac;
+    split_cell(fmaf(C.sv, (float)ks, C.fv0), bref, frac);
+    const float lo = frac - C.hv;  // lower edge, rows from bref: [-1, 0.5)
+    const int e0 = lo < -0.5f ? -1 : 0;
+    int r = bref + e0 - B0;          // tile row holding the lower edge
+    float d = ((float)e0 + 0.5f) - lo;  // to that row's upper edge: (0, 1]
+    const int rfirst = r;
+    float acc = 0.f;
+    float wz = fmaf((float)ks, g.dz, V.o[2]);
+    for (int kq = ks; kq <= ke; kq += 4) {
+        float xv[4];
+        ld4(cz + kq, xv);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float val = fp_amp<DD>(C, wz) * xv[t];
+            wz += g.dz;
+            const bool cross = d < w;
+            const float sum = fmaf(cross ? d : w, val, acc);
+            const float rest = (w - d) * val;
+            if (cross && (unsigned)r < (unsigned)BV) Z[r][tid] = sum;
+            acc = cross ? rest : sum;
+            r += cross ? 1 : 0;
+            d = (cross ? d + 1.f : d) - w;
+        }
+    }
+    if ((unsigned)r < (unsigned)BV) Z[r][tid] = acc;
+    for (int q = 0; q < min(rfirst, BV); ++q) Z[q][tid] = 0.f;
+    for (int q = max(r + 1, 0); q < BV; ++q) Z[q][tid] = 0.f;
+}
+
 // (with up to 4 cells per item the SF-TR, DD and voxel-driven kernels fit 80
 // registers: 3 blocks per SM)
 // TT: SF-TT (flat detector); the per-cell amplitude A2 is applied after the gather.
@@ -661,46 +710,27 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
 #pragma unroll
                 for (int r = 0; r < NA; ++r) S.Fu[r][tid] = Fu[r];
                 S.a0[tid] = C.aref + d0;
-#pragma unroll
-                for (int r = 0; r < BV; ++r) S.Z[r][tid] = 0.f;
-                if constexpr (TT) {
-                    tt_stage1<TIn, BV>(V, g, C, i, j, B0, bt, x, volZ, S.Z, tid);
-                } else {
                 // voxels whose axial rectangle can meet a row of the tile
-                const float hw = 0.5f + C.hv + kSearchPad;
+                const float hw = 0.5f + (TT ? V.m_tt_v : C.hv) + kSearchPad;
                 const float rsv = 1.f / C.sv;
                 const float ka = ((float)B0 - C.fv0 - hw) * rsv;
                 const float kb = ((float)(B0 + BV - 1) - C.fv0 + hw) * rsv;
                 const int k0 = max(0, (int)ceilf(fminf(ka, kb)));
                 const int k1 = min(g.nz - 1, (int)floorf(fmaxf(ka, kb)));
+                if (!TT && C.hv < 0.5f && C.sv > 0.f && volZ != nullptr && k0 <= k1) {
+                    // axial rectangle shorter than a row, column contiguous in
+                    // the z-major copy (nz a multiple of 4): one sweep down z
+                    const TIn *cz = volZ + (size_t)bt * g.nx * g.ny * g.nz + ((size_t)j * g.nx + i) * g.nz;
+                    sf_sweep<TIn, DD, BV>(C, g, V, cz, k0, k1, B0, S.Z, tid);
+                } else {
+#pragma unroll
+                for (int r = 0; r < BV; ++r) S.Z[r][tid] = 0.f;
+                if constexpr (TT) {
+                    tt_stage1<TIn, BV>(V, g, C, i, j, B0, bt, x, volZ, S.Z, tid);
+                } else {
                 const TIn *xc = x + (size_t)j * g.nx + i;
                 const size_t zs = (size_t)g.nx * g.ny;
-                if (C.hv < 0.5f && volZ != nullptr) {
-                    // axial rectangle shorter than a row (at most two rows per
-                    // voxel); the column is contiguous in the z-major copy and
-                    // is read 4 voxels per load (nz is a multiple of 4)
-                    const TIn *cz = volZ + (size_t)bt * g.nx * g.ny * g.nz + ((size_t)j * g.nx + i) * g.nz;
-                    for (int kb = k0 & ~3; kb <= k1; kb += 4) {
-                        float xv[4];
-                        ld4(cz + kb, xv);
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int k = kb + t;
-                            if (k < k0 || k > k1) continue;
-                            int bref;
-                            float vf;
-                            split_cell(fmaf(C.sv, (float)k, C.fv0), bref, vf);
-                            const float wz = fmaf((float)k, g.dz, V.o[2]);
-                            const float val = fp_amp<DD>(C, wz) * xv[t];
-                            int e0;
-                            float Fv0, Fv1;
-                            two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
-                            const int r0 = bref + e0 - B0;
-                            if (r0 >= 0 && r0 < BV) S.Z[r0][tid] = fmaf(Fv0, val, S.Z[r0][tid]);
-                            if (r0 + 1 >= 0 && r0 + 1 < BV) S.Z[r0 + 1][tid] = fmaf(Fv1, val, S.Z[r0 + 1][tid]);
-                        }
-                    }
-                } else if (C.hv < 0.5f) {
+                if (C.hv < 0.5f) {
                     // axial rectangle shorter than a row: at most two rows per voxel
 #pragma unroll 4
                     for (int k = k0; k <= k1; ++k) {
@@ -730,6 +760,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                                 S.Z[r][tid] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[r][tid]);
                         }
                     }
+                }
                 }
                 }
                 }
