@@ -363,17 +363,26 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                     Rs[e + 1][tid] = R;
                 }
                 for (int e = max(vb + 1, ef); e <= el + 1; ++e) Rs[e + 1][tid] = 0.f;
-                float fk = (float)kbeg;
+                // axial sweep: the voxels' rectangles [rel - hv, rel + hv]
+                // (rel = frac0 + sv kk) abut (sv = 2 hv < 1), so each voxel
+                // either lies in the current row e or crosses its upper edge
+                // once; d is the distance from its lower edge to that edge.
+                const float w = C.sv;
+                const float lo0 = frac0 - C.hv;
+                const int e0 = lo0 < -0.5f ? -1 : 0;  // == ef
+                float d = ((float)e0 + 0.5f) - lo0;
+                const float *rp = &Rs[e0 + 1][tid];
+                float wz = fmaf((float)kbeg, g.dz, V.o[2]);
 #pragma unroll
-                for (int kk = 0; kk < ZT; ++kk, fk += 1.f) {
+                for (int kk = 0; kk < ZT; ++kk) {
                     if (kbeg + kk < kend) {
-                        const float rel = fmaf(C.sv, (float)kk, frac0);
-                        int e0;
-                        float Fv0, Fv1;
-                        two_rows(rel - C.hv, rel + C.hv, e0, Fv0, Fv1);
-                        const float wz = fmaf(fk, g.dz, V.o[2]);
-                        acc[kk] = fmaf(RECON ? rw : fp_amp<DD>(C, wz), fmaf(Fv0, Rs[e0 + 1][tid], Fv1 * Rs[e0 + 2][tid]),
-                                       acc[kk]);
+                        const bool cross = d < w;
+                        const float f0 = cross ? d : w;
+                        const float sum = fmaf(f0, rp[0], (w - f0) * rp[128]);
+                        acc[kk] = fmaf(RECON ? rw : fp_amp<DD>(C, wz), sum, acc[kk]);
+                        rp += cross ? 128 : 0;
+                        d = (cross ? d + 1.f : d) - w;
+                        wz += g.dz;
                     }
                 }
                 continue;
