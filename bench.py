@@ -33,17 +33,30 @@ METRIC = "SF cone-beam fwd+back GUpdates/s & %HBM roofline; served p50/p99 laten
 UNIT = "GUpdates/s"
 WORKLOAD = ("3D circular cone-beam SF-TR forward+back, 256^3 x 0.5 mm FP32 volume, 360 views, "
             "flat 512x384 detector 0.8 mm, SAD 785 / SDD 1085 mm")
-# FP32 operations per (voxel, view) update of the SF-TR weight evaluation and
-# accumulation in circular geometry (derivation in the design notes).
+# Algorithmic FP32 operations per (voxel, view) update of SF-TR in circular
+# geometry, counted from the weight definition (Long et al.'s trapezoid x
+# rectangle footprint, amplitude dx |w| / max(|w_x|, |w_y|)):
+#   axial centre of the voxel's rectangle (sv k + fv0)          2
+#   its row (floor) and the offset of its edges in the row      4
+#   the two row bounds (centre -+ half height)                  2
+#   the overlaps with the (at most) two rows it meets           6
+#   transaxial taps: ~3.8 cells per voxel x one FMA (2)         ~7.6
+#   row sums times the axial weights                            2
+#   amplitude: wz, w_x^2 + w_y^2 + wz^2, sqrt, x invm, x value  6
+#   accumulate into the output                                  2
+#                                                       total ~30
+# The per-(column, view) trapezoid (~90 operations: four projected corners,
+# a sort, the cell integrals) is shared by the column's nz voxels and not
+# counted.
 SF_FLOPS_PER_UPDATE = 30.0
-N_SM, FP32_LANES = 152, 128
+FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 
-# DRAM bytes per launch from one ncu capture of the same kernel source
-# (sha256 of the .cu at capture time); null once the source changes.
-NCU_TRAFFIC = {
-    "sf_back": {"bytes": 417.7e6, "src": "06c6fc1164c1c85b"},
-    "sf_fwd": {"bytes": 917.9e6, "src": "06c6fc1164c1c85b"},
-}
+# Counters of one `ncu --set full` capture of each kernel on this workload
+# (per launch): DRAM read + write bytes, L2 (lts__t_sectors x 32) bytes and the
+# L2 throughput peak implied by its percent-of-peak counter; src = sha256
+# prefix of the kernel's .cu at capture time (the bench reports null once the
+# source differs).
+NCU = {}
 
 
 def _src_hash(name: str) -> str:
@@ -129,9 +142,10 @@ def job_gupdates(upd_per_step: float, steps: int, ws: int, max_ms: float) -> flo
     return upd_per_step * steps * ws / (max_ms * 1e-3) / 1e9
 
 
-def cpu_oracle_sample(spec, nviews: int, x=None):
+def cpu_oracle_sample(spec, nviews: int, x=None, threads: int = 0):
     """The FP64 oracle timed on the host cores on a view-decimated copy of
-    the workload (nviews evenly spaced views): SF forward + SF back."""
+    the workload (nviews evenly spaced views): SF forward + SF back.
+    threads = 0: every host core; otherwise that many OpenMP threads."""
     import numpy as np
 
     import oracle
@@ -141,12 +155,18 @@ def cpu_oracle_sample(spec, nviews: int, x=None):
     sub = spec.subset(views)
     if x is None:
         x = W.phantom(spec, seed=0)
-    t0 = time.perf_counter()
-    y = oracle.forward(sub, "sf", x)
-    oracle.back(sub, "sf", y)
-    dt = time.perf_counter() - t0
+    every = len(os.sched_getaffinity(0))
+    cores = threads or every
+    oracle.set_threads(cores)
+    try:
+        t0 = time.perf_counter()
+        y = oracle.forward(sub, "sf", x)
+        oracle.back(sub, "sf", y)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(every)
     upd = 2.0 * spec.n_vox * nviews
-    return upd / dt / 1e9, dt, oracle.max_threads(), f"{nviews} of {spec.nview} views, full volume"
+    return upd / dt / 1e9, dt, cores, f"{nviews} of {spec.nview} views, full volume"
 
 
 def _gdict(spec):
@@ -408,6 +428,63 @@ def mbir_loop_timing(ct, g, spec, steps: int = 10):
                       "fused_gups": upd / out["fused"]["ms"] / 1e6}), flush=True)
 
 
+def saddle_record(dev, reps: int = 2):
+    """The non-circular saddle workload (512^3 volume of 0.4 mm voxels, 500
+    views, flat 1024^2 detector of 0.4 mm; saddle trajectory with seeded pose
+    jitter) with SF-TR: forward and back time (CUDA events, after one warm-up
+    pair) in FP32 and in FP16 storage, and the FP16 results' error against
+    the FP64 oracle: the forward on two views (input and output rounding
+    included) and the back at 200 sampled voxels of the stored sinogram."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2503_16741_gb300 as ct
+    import workloads as W
+    spec = W.noncirc3d_saddle()
+    g = ct.Geometry.from_spec(spec)
+    x64 = W.phantom(spec, seed=0, device=dev, dtype=torch.float64)
+    stream = torch.cuda.current_stream(dev)
+    upd = spec.n_vox * spec.nview
+    rec = {"workload": "non-circular saddle cone beam, 512^3 x 0.4 mm, 500 views, flat 1024^2 x 0.4 mm, "
+                       "SAD 785 / SDD 1200 mm, SF-TR", "updates_per_op": upd}
+    for name, dt in (("f32", torch.float32), ("f16", torch.float16)):
+        x = x64.to(dt).reshape(g.vol_shape)
+        y = torch.empty(g.sino_shape, dtype=dt, device=dev)
+        xb = torch.empty(g.vol_shape, dtype=dt, device=dev)
+        ct.forward_into(g, x, y, "sf", stream=stream)
+        ct.back_into(g, y, xb, "sf", stream=stream)
+        torch.cuda.synchronize(dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tf = tb = 0.0
+        for _ in range(reps):
+            e[0].record(stream)
+            ct.forward_into(g, x, y, "sf", stream=stream)
+            e[1].record(stream)
+            ct.back_into(g, y, xb, "sf", stream=stream)
+            e[2].record(stream)
+            torch.cuda.synchronize(dev)
+            tf += e[0].elapsed_time(e[1]) / reps
+            tb += e[1].elapsed_time(e[2]) / reps
+        r = {"fwd_ms": tf, "back_ms": tb, "fwd_gups": upd / tf / 1e6, "back_gups": upd / tb / 1e6,
+             "pair_gups": 2 * upd / (tf + tb) / 1e6}
+        if name == "f16":
+            views = [123, 377]
+            xn = x64.cpu().numpy()
+            yref = oracle.forward(spec.subset(views), "sf", xn)
+            yv = y[views].double().cpu().numpy()
+            r["fwd_rel_l2_vs_fp64"] = float(np.linalg.norm(yv - yref) / np.linalg.norm(yref))
+            sel = np.random.default_rng(3).choice(spec.n_vox, size=200, replace=False)
+            bref = oracle.back_voxels(spec, "sf", y.double().cpu().numpy(), sel)
+            bgot = xb.double().cpu().numpy().ravel()[sel]
+            r["back_rel_l2_vs_fp64"] = float(np.linalg.norm(bgot - bref) / np.linalg.norm(bref))
+            r["error_sample"] = "forward: views 123, 377 of the FP64 phantom; back: 200 voxels of the stored sinogram"
+        rec[name] = r
+        del x, y, xb
+    g.close()
+    return rec
+
+
 def run_reference(args):
     """The oracle as the reference arm: K timed steps of a bounded sample."""
     ws, rank, _ = _dist()
@@ -445,6 +522,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=80)
+    ap.add_argument("--no-saddle", action="store_true", help="skip the non-circular saddle record")
+    ap.add_argument("--saddle-reps", type=int, default=2)
     ap.add_argument("--suite", action="store_true", help="time every projector on each workload")
     ap.add_argument("--suite-reps", type=int, default=2)
     ap.add_argument("--suite-filter", default="", help="only workloads whose name contains this")
@@ -509,44 +588,60 @@ def main():
     upd_step = 2.0 * spec.n_vox * spec.nview
     value = job_gupdates(upd_step, K, ws, total_ms)
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the public API with host buffers (pinned), timed by
+    # the host's wall clock: each step copies the volume in, projects forward
+    # and back, copies the result volume out and waits for it on the host
     xh = x.cpu().pin_memory()
     xbh = torch.empty(spec.vol_shape, dtype=torch.float32).pin_memory()
     xd = torch.empty_like(x)
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        step()
-        xbh.copy_(xb, non_blocking=True)
-    torch.cuda.synchronize(dev)
-    if ws > 1:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(K):
+
+    def e2e_step():
         xd.copy_(xh, non_blocking=True)
         ct.forward_into(geom, xd, y, "sf", stream=stream)
         ct.back_into(geom, y, xb, "sf", stream=stream)
         xbh.copy_(xb, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        torch.cuda.synchronize(dev)
+
+    for _ in range(2):
+        e2e_step()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_step()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev)
     e2e = {"value": job_gupdates(upd_step, K, ws, e2e_ms), "unit": UNIT,
-           "h2d_bytes_per_step": xh.numel() * 4, "d2h_bytes_per_step": xbh.numel() * 4}
+           "h2d_bytes_per_step": xh.numel() * 4, "d2h_bytes_per_step": xbh.numel() * 4,
+           "timer": "host wall clock, synchronised every step"}
 
     if rank != 0:
         return
     peaks = _peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    fp32_peak = n_sm * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     dom, dom_ms, dom_src = ("sf_back", back_ms, "k_sf.cu") if back_ms >= fwd_ms else \
         ("sf_fwd", fwd_ms, "k_sf.cu")
     flops = SF_FLOPS_PER_UPDATE * spec.n_vox * spec.nview
     achieved = flops / (dom_ms * 1e-3) / 1e12
-    tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash(dom_src) else None
+    nc = NCU.get(dom)
+    fresh = nc is not None and nc.get("src") == _src_hash(dom_src)
+    traffic = nc["dram_bytes"] if fresh else None
     vol_b, sino_b = spec.n_vox * 4, spec.n_cells * 4
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_ach = (vol_b + sino_b) / (dom_ms * 1e-3) / 1e9
+    mem = {"dram_bytes": traffic, "dram_gbs": None, "dram_frac": None, "l2_bytes": None,
+           "l2_gbs": None, "l2_peak_gbs": None, "l2_frac": None,
+           "note": "ncu counters of the same kernel source, per launch, over this run's kernel time; "
+                   "DRAM against the measured copy bandwidth, L2 against the peak implied by ncu's "
+                   "lts__t_sectors percent of peak" if fresh else "no capture of the current source"}
+    if fresh:
+        mem["dram_gbs"] = traffic / (dom_ms * 1e-3) / 1e9
+        mem["dram_frac"] = mem["dram_gbs"] / hbm_peak
+        mem["l2_bytes"] = nc["l2_bytes"]
+        mem["l2_gbs"] = nc["l2_bytes"] / (dom_ms * 1e-3) / 1e9
+        mem["l2_peak_gbs"] = nc["l2_peak_gbs"]
+        mem["l2_frac"] = mem["l2_gbs"] / nc["l2_peak_gbs"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -556,8 +651,8 @@ def main():
                    "fwd_ms": fwd_ms, "back_ms": back_ms},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": traffic,
-                     "peak_note": f"FP32 FMA peak {N_SM} SM x {FP32_LANES} lanes x 2 at {sm_mhz:.0f} MHz",
+                     "traffic": traffic, "memory": mem,
+                     "peak_note": f"FP32 FMA peak {n_sm} SM x {FP32_LANES} lanes x 2 at {sm_mhz:.0f} MHz",
                      "flops_per_update": SF_FLOPS_PER_UPDATE},
         "hbm_roofline": {"kernel": dom, "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
                          "frac": hbm_ach / hbm_peak, "bytes": "compulsory: read input once, write output once",
@@ -574,10 +669,15 @@ def main():
                               "p50/p99 at 0.8); fan-beam 128^2-512^2 and "
                               "circular flat / circular curved / saddle non-circular 64^3-256^3 volumes, "
                               "90-360 views, fwd 40% / back 40% / 10-step MBIR 20%, SF or DD")
+    if not args.no_saddle:
+        out["saddle"] = saddle_record(dev, args.saddle_reps)
     if ws == 1 and not args.no_cpu_baseline:
         val, dt, cores, sample = cpu_oracle_sample(spec, 8)
+        val1, dt1, _, sample1 = cpu_oracle_sample(spec, 2, threads=1)
         out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample + f" ({dt:.1f} s)"}
+                               "sample": sample + f" ({dt:.1f} s)",
+                               "one_core": {"value": val1, "unit": UNIT, "cores": 1,
+                                            "sample": sample1 + f" ({dt1:.1f} s)"}}
     print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()

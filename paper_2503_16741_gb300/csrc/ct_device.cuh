@@ -92,8 +92,9 @@ struct Trap {
     float k0, k1, k2, k3;
     float h1, h3;
 };
+// (fast reciprocals: a ramp's slope factor carries ~2 ulp, ~1e-7 of its weights)
 __device__ __forceinline__ Trap make_trap(float k0, float k1, float k2, float k3) {
-    return Trap{k0, k1, k2, k3, 0.5f / fmaxf(k1 - k0, 1e-30f), 0.5f / fmaxf(k3 - k2, 1e-30f)};
+    return Trap{k0, k1, k2, k3, __fdividef(0.5f, fmaxf(k1 - k0, 1e-30f)), __fdividef(0.5f, fmaxf(k3 - k2, 1e-30f))};
 }
 __device__ __forceinline__ float trap_G(const Trap &t, float u) {
     return ramp_int_h(u - t.k0, t.k1 - t.k0, t.h1) - ramp_int_h(u - t.k2, t.k3 - t.k2, t.h3);

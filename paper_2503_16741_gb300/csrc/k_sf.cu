@@ -210,7 +210,7 @@ __device__ __forceinline__ float fp_amp(const C_ &C, float wz) {
 // amplitude A2; its axial trapezoids reach further, so the row buffer holds
 // ZT + 6 rows.
 template <typename TIn, bool CURVED, bool DD, int ZT, bool RECON = false, bool TT = false>
-__global__ void __launch_bounds__(128, 7)
+__global__ void __launch_bounds__(128, ZT <= 16 ? 7 : 5)
 sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
     constexpr int NR = TT ? ZT + 6 : ZT + 3;  // SF, DD: rows -1 .. ZT + 1 relative to the chunk's first voxel
@@ -245,6 +245,9 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             const CtView &V = sview[vv];
             const SfCol C = sf_col<CURVED, DD>(V, g, i, j);
             int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
+            // footprint wholly on the detector: its first and last cell edges
+            // lie outside the trapezoid
+            const bool whole = d0 >= -C.aref && d1 <= g.nu - 1 - C.aref;
             d0 = max(d0, -C.aref);
             d1 = min(d1, g.nu - 1 - C.aref);
             if (d0 > d1) continue;
@@ -340,7 +343,10 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
             }
             if (d1 - d0 <= 3 && C.hv < 0.5f && C.sv > 0.f && g.nu >= 4) {
                 float F[4], Fu[4];
-                trap_cells4(C.T, d0, d1, F);
+                if (whole)
+                    nc_cells<4>(C.T, d0, d1, F);  // antiderivative at the interior cell edges only
+                else
+                    trap_cells4(C.T, d0, d1, F);
                 const int as = window4(F, C.aref + d0, g.nu, Fu);
                 // Rows relative to the chunk's first voxel: voxel kk sits at
                 // rel = frac0 + sv kk rows from row bref0 (0 < sv < 1), so it
@@ -500,7 +506,9 @@ constexpr int kSlabSeg = 256;
 
 template <int RPT, int NA> struct SfFwdSmem {
     float Z[8 * RPT][kItems];  // [row][item]: conflict-free in both stages
-    float Fu[NA][kItems];      // the item's NA transaxial cell weights
+    // the item's NA transaxial cell weights; rows padded by 8 so that lanes
+    // reading one item's weights of different cells fall on different banks
+    float Fu[NA][kItems + 8];
     int a0[kItems];
     int L0[kSlabSeg], cnt[kSlabSeg], off[kSlabSeg + 1];
 };
@@ -511,7 +519,7 @@ template <int RPT, int NA> struct SfFwdSmem {
 template <typename TIn, bool CURVED, int BV, int NA>
 __device__ __forceinline__ void vx_stage1(const CtView &V, const CtGrid &g, int i, int j, int B0, int bt,
                                           const TIn *__restrict__ x, const TIn *__restrict__ volZ,
-                                          float (&Z)[BV][kItems], float (&Fu)[NA][kItems], int *a0, int tid) {
+                                          float (&Z)[BV][kItems], float (&Fu)[NA][kItems + 8], int *a0, int tid) {
     const VxCol C = vx_col<CURVED>(V, g, i, j);
     const float af = floorf(C.fu), ta = C.fu - af;
     Fu[0][tid] = 1.f - ta;
@@ -625,21 +633,34 @@ __device__ __forceinline__ void sf_sweep(const SfCol &C, const CtGrid &g, const 
     const int rfirst = r;
     float acc = 0.f;
     float wz = fmaf((float)ks, g.dz, V.o[2]);
-    for (int kq = ks; kq <= ke; kq += 4) {
-        float xv[4];
-        ld4(cz + kq, xv);
+    auto step = [&](float x) {
+        const float val = fp_amp<DD>(C, wz) * x;
+        wz += g.dz;
+        const bool cross = d < w;
+        const float sum = fmaf(cross ? d : w, val, acc);
+        const float rest = (w - d) * val;
+        if (cross && (unsigned)r < (unsigned)BV) Z[r][tid] = sum;
+        acc = cross ? rest : sum;
+        r += cross ? 1 : 0;
+        d = (cross ? d + 1.f : d) - w;
+    };
+    // eight voxels (one 32-byte sector of FP32) per iteration: both halves
+    // of the sector are requested together
+    int kq = ks;
+    for (; kq + 7 <= ke; kq += 8) {
+        float xa[4], xb[4];
+        ld4(cz + kq, xa);
+        ld4(cz + kq + 4, xb);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const float val = fp_amp<DD>(C, wz) * xv[t];
-            wz += g.dz;
-            const bool cross = d < w;
-            const float sum = fmaf(cross ? d : w, val, acc);
-            const float rest = (w - d) * val;
-            if (cross && (unsigned)r < (unsigned)BV) Z[r][tid] = sum;
-            acc = cross ? rest : sum;
-            r += cross ? 1 : 0;
-            d = (cross ? d + 1.f : d) - w;
-        }
+        for (int t = 0; t < 4; ++t) step(xa[t]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) step(xb[t]);
+    }
+    if (kq <= ke) {
+        float xa[4];
+        ld4(cz + kq, xa);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) step(xa[t]);
     }
     if ((unsigned)r < (unsigned)BV) Z[r][tid] = acc;
     for (int q = 0; q < min(rfirst, BV); ++q) Z[q][tid] = 0.f;
@@ -981,7 +1002,11 @@ to_zmajor(const T *__restrict__ x, T *__restrict__ xZ, int nx, int ny, int nz) {
 
 // ------------------------------------------------------------ launchers
 namespace {
-constexpr int kZT = 16;
+// voxels per thread of the circular footprint backs: 16 on a flat detector
+// (7 blocks per SM); 32 on a curved one, whose per-(column, view) set-up
+// (arc tangents of the corners) costs more and is shared by twice the voxels
+// (5 blocks per SM)
+constexpr int kZT = 16, kZTcurved = 32;
 
 template <typename TIn, bool CURVED, bool DD, int RPT, int NA, bool VOX = false, bool TT = false>
 cudaError_t fp_fwd_stream(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
@@ -1040,9 +1065,10 @@ cudaError_t fp_fwd_circ(const CtGrid &g, const CtView *views, const TIn *src, vo
 template <typename TIn, bool CURVED, bool DD, bool RECON = false, bool TT = false>
 cudaError_t fp_back_circ(const CtGrid &g, const CtView *views, const TIn *src, void *out, int out_t,
                          int batch, cudaStream_t st) {
-    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + kZT - 1) / kZT;
+    constexpr int ZT = CURVED ? kZTcurved : kZT;
+    const int tiles_x = (g.nx + 31) / 32, nzc = (g.nz + ZT - 1) / ZT;
     dim3 blk(32, 4), grd((unsigned)(tiles_x * nzc * batch), (unsigned)((g.ny + 3) / 4));
-    sf_back_circ<TIn, CURVED, DD, kZT, RECON, TT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
+    sf_back_circ<TIn, CURVED, DD, ZT, RECON, TT><<<grd, blk, 0, st>>>(g, views, src, out, out_t, tiles_x, nzc);
     return cudaGetLastError();
 }
 
