@@ -176,82 +176,119 @@ def _gdict(spec):
                                           "u_ofst", "v_ofst")}
 
 
+SERVE_SIZES = (64, 128, 256, 384, 512)
+SERVE_SIZE_P = (0.3, 0.3, 0.2, 0.12, 0.08)
+SERVE_VIEWS = (90, 180, 360, 720)
+
+
 def serving_mix(n_req: int, seed: int = 0):
-    """Requests mixing the four geometry kinds, volumes of 64^3-256^3 (2D:
-    128^2-512^2), 90-360 views, and fwd (40 %) / back (40 %) / 10-step MBIR
-    (20 %) with the SF or DD projector; (request, voxel-view updates)."""
+    """The serving workload: Poisson-arriving requests over the four geometry
+    kinds (2D fan beam, circular flat, circular curved, saddle non-circular),
+    volumes of 64^3-512^3 (P = 0.3, 0.3, 0.2, 0.12, 0.08; fan beam: (2n)^2
+    images; curved: n^2 x n/4, the curved workload's shape), 90 / 180 / 360 /
+    720 views, detectors covering the volume (about 2n x 1.5n cells), forward
+    40 % / back 40 % / 10-step least-squares MBIR 20 %, SF or DD.  Bounded so
+    that 500 requests run in tens of seconds: MBIR volumes at most 256^3
+    (non-circular 128^3), non-circular volumes at most 256^3 (the
+    non-circular kernels take about ten times longer per update).
+    Returns [(request fields, voxel-view updates)]."""
     import numpy as np
 
     import workloads as W
-    from paper_2503_16741_gb300.serve import Request
     rng = np.random.default_rng(seed)
-    kinds = [("fan2d", W.fan2d_small(360)), ("circ", W.circ3d_256()), ("curved", W.circ3d_curved()),
-             ("noncirc", W.noncirc3d_saddle(360))]
+    bases = {"fan2d": W.fan2d_small(720), "circ": W.circ3d_256(720), "curved": W.circ3d_curved(),
+             "noncirc": W.noncirc3d_saddle(720)}
+    names = list(bases)
     out = []
     for _ in range(n_req):
-        name, base = kinds[rng.integers(4)]
-        views = int(rng.choice([90, 180, 360]))
-        if name == "fan2d":
-            spec = W.scaled(base, int(rng.choice([128, 256, 512])), views)
-        else:
-            spec = W.scaled(base, int(rng.choice([64, 128, 256])), views)
-        op = rng.choice(["fwd", "back", "mbir"], p=[0.4, 0.4, 0.2])
+        name = names[rng.integers(4)]
+        n = int(rng.choice(SERVE_SIZES, p=SERVE_SIZE_P))
+        views = int(rng.choice(SERVE_VIEWS))
+        op = str(rng.choice(["fwd", "back", "mbir"], p=[0.4, 0.4, 0.2]))
+        cap = (128 if op == "mbir" else 256) if name == "noncirc" else (256 if op == "mbir" else 512)
+        n = min(n, cap)
+        spec = W.scaled(bases[name], 2 * n if name == "fan2d" else n, views)
         proj = str(rng.choice(["sf", "dd"]))
-        vol = (spec.ny, spec.nx) if spec.kind == "fan2d" else spec.vol_shape
-        sino = (spec.nview, spec.nu) if spec.kind == "fan2d" else spec.sino_shape
-        data = rng.random(vol if op == "fwd" else sino, dtype=np.float32)
         passes = 1 if op != "mbir" else 20
-        out.append((Request(_gdict(spec), str(op), data, projector=proj, iters=10),
+        out.append(({"geometry": _gdict(spec), "op": op, "projector": proj, "iters": 10, "spec": spec},
                     passes * spec.n_vox * spec.nview))
     return out
 
 
-def serving_bench(dev_index: int, n_req: int, dtype: str = "f32"):
-    """Closed-loop saturation, then open-loop Poisson arrivals at 0.5, 0.8 and
-    0.95 of it."""
+def serving_bench(dev_index: int, n_req: int, dtype: str, budget: int, loads=(0.9,), n_err: int = 4):
+    """Closed-loop saturation, then open-loop Poisson arrivals at the given
+    fractions of it, with device-resident inputs and results.  Also the error
+    of sampled small results against the FP64 oracle."""
     import numpy as np
+    import torch
 
-    from paper_2503_16741_gb300.serve import GpuExecutor, Server, drive, poisson_arrivals
+    import oracle
+    from paper_2503_16741_gb300.serve import GpuExecutor, Request, Server, drive, poisson_arrivals
     mix = serving_mix(n_req)
-    for r, _ in mix:
-        r.dtype = dtype
+    dev = torch.device("cuda", dev_index)
+    T = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    gen = torch.Generator(device=dev).manual_seed(0)
+    reqs = []
+    for f, _ in mix:
+        spec = f["spec"]
+        vol = (spec.ny, spec.nx) if spec.kind == "fan2d" else spec.vol_shape
+        sino = (spec.nview, spec.nu) if spec.kind == "fan2d" else spec.sino_shape
+        shape = vol if f["op"] == "fwd" else sino
+        data = torch.rand(shape, generator=gen, device=dev).to(T)  # resident before timing
+        reqs.append(Request(f["geometry"], f["op"], data, projector=f["projector"], dtype=dtype,
+                            iters=f["iters"], out_device=True))
     ex = GpuExecutor(dev_index, slots=4)
-    for r, _ in mix:  # geometries and MBIR step sizes resident before timing
+    for r in reqs:  # geometries and MBIR step sizes resident before timing
         ex.geometry(r.geometry)
         if r.op == "mbir":
             ex.step_size(r.geometry, r.projector)
-    srv = Server(hbm_budget=48 << 30, max_batch=4, executor=ex)
-    warm = [srv.submit(r) for r, _ in mix[:8]]
-    for f in warm:
-        f.result(timeout=300)
+    budget = max(budget, max(ex.request_bytes(r) for r in reqs))  # every request admissible
+    srv = Server(hbm_budget=budget, max_batch=4, executor=ex)
+    for fut in [srv.submit(r) for r in reqs[:8]]:
+        fut.result(timeout=600)
     t0 = time.perf_counter()
-    futs = [srv.submit(r) for r, _ in mix]
-    for f in futs:
-        f.result(timeout=300)
+    futs = [srv.submit(r) for r in reqs]
+    for fut in futs:
+        fut.result(timeout=600)
     t_sat = time.perf_counter() - t0
+    st_sat = srv.stats()
     srv.close()
     sat_rps = n_req / t_sat
     upd = sum(u for _, u in mix)
-    loads = {}
-    for load in (0.5, 0.8, 0.95):  # open loop at these fractions of saturation
-        srv = Server(hbm_budget=48 << 30, max_batch=4, executor=ex)
+    by_load = []
+    for load in loads:
+        srv = Server(hbm_budget=budget, max_batch=4, executor=ex)
         arr = poisson_arrivals(load * sat_rps, n_req, seed=1)
         t0 = time.perf_counter()
-        futs = drive(srv, [r for r, _ in mix], arr)
-        for f in futs:
-            f.result(timeout=300)
+        futs = drive(srv, reqs, arr)
+        outs = [fut.result(timeout=600) for fut in futs]
         t_open = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
-        loads[load] = {"load": load, "offered_req_per_s": load * sat_rps, "served_req_per_s": n_req / t_open,
-                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "launches": st["launches"],
-                       "hbm_peak_bytes": st["hbm_peak_bytes"]}
-    main = loads[0.8]
-    return {"dtype": dtype, "requests": n_req, "saturation_req_per_s": sat_rps,
-            "saturation_gupdates_per_s": upd / t_sat / 1e9,
+        by_load.append({"load": load, "offered_req_per_s": load * sat_rps, "served_req_per_s": n_req / t_open,
+                        "served_gupdates_per_s": upd / t_open / 1e9, "p50_ms": st["p50_ms"],
+                        "p99_ms": st["p99_ms"], "launches": st["launches"], "hbm_peak_bytes": st["hbm_peak_bytes"],
+                        "memory_waits": st["memory_waits"]})
+    # error of sampled small results against FP64 (the oracle on the stored inputs)
+    errs = []
+    for k, (f, _) in enumerate(mix):
+        spec = f["spec"]
+        if len(errs) >= n_err or f["op"] not in ("fwd", "back") or spec.n_vox * spec.nview > 3e8:
+            continue
+        x = reqs[k].data.double().cpu().numpy()
+        ref = (oracle.forward if f["op"] == "fwd" else oracle.back)(spec, f["projector"],
+                                                                    x.reshape((1,) + x.shape))
+        got = outs[k].double().cpu().numpy().reshape(ref.shape)
+        errs.append({"request": k, "kind": spec.kind, "det": spec.det, "op": f["op"], "projector": f["projector"],
+                     "n": spec.nx, "views": spec.nview,
+                     "rel_l2_vs_fp64": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))})
+    main = by_load[-1]
+    return {"dtype": dtype, "requests": n_req, "hbm_budget_bytes": budget,
+            "saturation_req_per_s": sat_rps, "saturation_gupdates_per_s": upd / t_sat / 1e9,
+            "saturation_memory_waits": st_sat["memory_waits"], "saturation_hbm_peak_bytes": st_sat["hbm_peak_bytes"],
             "offered_req_per_s": main["offered_req_per_s"], "served_req_per_s": main["served_req_per_s"],
-            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "launches": main["launches"],
-            "hbm_peak_bytes": main["hbm_peak_bytes"], "by_load": list(loads.values())}
+            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "by_load": by_load,
+            "error_vs_fp64": errs, "max_rel_l2_vs_fp64": max((e["rel_l2_vs_fp64"] for e in errs), default=None)}
 
 
 def run_suite(args):
@@ -521,7 +558,10 @@ def main():
     ap.add_argument("--ref-views", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=80)
+    ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--serve-budget-gib", type=float, default=5.0,
+                    help="admission budget, GiB (5: just above the largest FP32 request of the mix)")
+    ap.add_argument("--serve-loads", default="0.9", help="open-loop loads, fractions of saturation (comma list)")
     ap.add_argument("--no-saddle", action="store_true", help="skip the non-circular saddle record")
     ap.add_argument("--saddle-reps", type=int, default=2)
     ap.add_argument("--suite", action="store_true", help="time every projector on each workload")
@@ -663,12 +703,15 @@ def main():
     }
     if not args.no_serving:
         torch.cuda.synchronize(dev)
-        out["serving"] = [serving_bench(local, args.serve_requests, "f32"),
-                          serving_bench(local, args.serve_requests, "f16")]
-        out["serving_mix"] = ("Poisson arrivals at 0.5 / 0.8 / 0.95 x measured saturation (top-level "
-                              "p50/p99 at 0.8); fan-beam 128^2-512^2 and "
-                              "circular flat / circular curved / saddle non-circular 64^3-256^3 volumes, "
-                              "90-360 views, fwd 40% / back 40% / 10-step MBIR 20%, SF or DD")
+        budget = int(args.serve_budget_gib * (1 << 30))
+        loads = tuple(float(v) for v in args.serve_loads.split(","))
+        out["serving"] = [serving_bench(local, args.serve_requests, "f32", budget, loads),
+                          serving_bench(local, args.serve_requests, "f16", budget, loads)]
+        out["serving_mix"] = (serving_mix.__doc__.split("Returns")[0].strip().replace("\n    ", " ")
+                              + " Inputs and results device-resident; open-loop Poisson arrivals at "
+                              f"{args.serve_loads} of the measured closed-loop saturation (top-level figures at "
+                              f"the last); the same {args.serve_budget_gib:g} GiB admission budget (request "
+                              "buffers, temporaries and library workspace) for both storage types.")
     if not args.no_saddle:
         out["saddle"] = saddle_record(dev, args.saddle_reps)
     if ws == 1 and not args.no_cpu_baseline:

@@ -22,13 +22,17 @@
  * stream-ordered workspace from a library-owned memory pool on the current
  * device (kept in the pool between calls, so steady-state calls do not reach
  * the driver's allocator) and return it on the same stream:
- *   ct_back with CT_DD or CT_SF_TT: the sinogram scaled by each cell's
- *     path length or amplitude, batch x nview x nv x nu floats;
+ *   ct_back with CT_DD or CT_SF_TT, and with CT_RAY in circular geometry:
+ *     the sinogram scaled by each cell's path length, amplitude or secant,
+ *     batch x nview x nv x nu floats (non-circular CT_DD only when its
+ *     footprints fit the footprint kernels, at most 8 cells by 4 rows);
  *   ct_forward with CT_SF or CT_DD (circular geometry with nz a multiple
  *     of 4 and at least 8, or non-circular geometry), with CT_SF_TT, and
  *     with CT_VOXEL (the same circular cases): a z-major copy of the volume,
  *     batch x nz x ny x nx elements of in_t (skipped, at some speed, when it
  *     cannot be had).
+ * ct_workspace_bytes gives that size for a call; ct_workspace_limit caps
+ * what the pool keeps once calls have returned it.
  * Results are deterministic: no atomics, fixed summation order.
  *
  * Errors: each call returns a ct_status; ct_last_error() gives a message for
@@ -36,6 +40,8 @@
  */
 #ifndef CTPROJ_H
 #define CTPROJ_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -241,6 +247,29 @@ ct_status ct_back_dd_noalloc(const ct_geometry *geom, ct_dtype in_t, const void 
  *   filter's name only; the form above is Kak & Slaney's. */
 ct_status ct_ramp_filter(const ct_geometry *geom, ct_dtype in_t, const void *sino, ct_dtype out_t, void *out,
                          int batch, void *cuda_stream);
+
+/* Pooled workspace (bytes) that one ct_forward (direction 0) or ct_back
+ * (direction 1) call with these arguments takes from the library's pool on
+ * top of the caller's buffers (see the list at the top of this header; the
+ * paper has no counterpart: this is the memory accounting a server needs to
+ * admit requests by a device-memory budget).  Host-only; *bytes = 0 when the
+ * call takes none.  Errors: CT_ERR_INVALID_ARG for null pointers, unknown
+ * enums, a direction other than 0 / 1 or batch < 1. */
+ct_status ct_workspace_bytes(const ct_geometry *geom, ct_projector proj, ct_mode mode, int direction,
+                             ct_dtype in_t, int batch, size_t *bytes);
+
+/* Caps the bytes the current device's pool keeps once calls have returned
+ * their workspace: blocks above `bytes` go back to the device at the next
+ * synchronisation, and what the pool already holds above it is released now
+ * (blocks in use are not affected).  Default: the pool keeps everything.
+ * Errors: CT_ERR_CUDA if the pool cannot be created or set. */
+ct_status ct_workspace_limit(size_t bytes);
+
+/* Current device's pool: bytes it holds from the device now (reserved) and
+ * the high-water mark of the bytes in use by projection calls since the last
+ * reset (used_high); reset_high != 0 resets that mark to zero after reading
+ * it.  Either output pointer may be NULL.  Errors: CT_ERR_CUDA. */
+ct_status ct_workspace_usage(size_t *reserved, size_t *used_high, int reset_high);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char *ct_last_error(void);

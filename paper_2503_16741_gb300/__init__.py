@@ -8,7 +8,9 @@ include/ctproj.h; this package marshals PyTorch tensors to it.
 """
 from .autograd import Projector, ProjectorFn
 from .binding import (CTError, Geometry, back, back_acc, back_dd_noalloc, back_into, fbp, forward,
-                      forward_acc, forward_into, lib_path, load, ramp_filter)
+                      forward_acc, forward_into, lib_path, load, ramp_filter, workspace_bytes, workspace_limit,
+                      workspace_usage)
 
 __all__ = ["Geometry", "forward", "back", "forward_into", "back_into", "forward_acc", "back_acc",
-           "back_dd_noalloc", "ramp_filter", "fbp", "ProjectorFn", "Projector", "CTError", "load", "lib_path"]
+           "back_dd_noalloc", "ramp_filter", "fbp", "workspace_bytes", "workspace_limit", "workspace_usage",
+           "ProjectorFn", "Projector", "CTError", "load", "lib_path"]

@@ -93,6 +93,13 @@ def load():
         lib.ct_back_dd_noalloc.restype = C.c_int
         lib.ct_ramp_filter.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
         lib.ct_ramp_filter.restype = C.c_int
+        lib.ct_workspace_bytes.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                           P(C.c_size_t)]
+        lib.ct_workspace_bytes.restype = C.c_int
+        lib.ct_workspace_limit.argtypes = [C.c_size_t]
+        lib.ct_workspace_limit.restype = C.c_int
+        lib.ct_workspace_usage.argtypes = [P(C.c_size_t), P(C.c_size_t), C.c_int]
+        lib.ct_workspace_usage.restype = C.c_int
         lib.ct_last_error.restype = C.c_char_p
         lib.ct_version.restype = C.c_char_p
         for f in ("ct_geometry_create", "ct_geometry_destroy", "ct_geometry_shape", "ct_forward", "ct_back"):
@@ -326,3 +333,27 @@ def back_dd_noalloc(geom: Geometry, y: torch.Tensor, out_dtype: Optional[torch.d
     _check(load().ct_back_dd_noalloc(geom.handle, DTYPES[y.dtype], y.data_ptr(), DTYPES[x.dtype],
                                      x.data_ptr(), b, _stream_ptr(stream)))
     return x
+
+
+def workspace_bytes(geom: Geometry, projector: str, direction: str, dtype: torch.dtype = torch.float32,
+                    batch: int = 1, mode: str = "proj") -> int:
+    """Pooled workspace (bytes) one forward ('fwd') or back ('back') call
+    takes from the library on top of its input and output (ct_workspace_bytes)."""
+    out = C.c_size_t(0)
+    _check(load().ct_workspace_bytes(geom.handle, PROJECTORS[projector], MODES[mode],
+                                     {"fwd": 0, "back": 1}[direction], DTYPES[dtype], int(batch), C.byref(out)))
+    return int(out.value)
+
+
+def workspace_limit(nbytes: int) -> None:
+    """Cap what the current device's workspace pool keeps between calls
+    (ct_workspace_limit)."""
+    _check(load().ct_workspace_limit(int(nbytes)))
+
+
+def workspace_usage(reset_high: bool = False):
+    """(bytes the pool holds now, high-water mark of bytes in use since the
+    last reset) for the current device (ct_workspace_usage)."""
+    r, h = C.c_size_t(0), C.c_size_t(0)
+    _check(load().ct_workspace_usage(C.byref(r), C.byref(h), 1 if reset_high else 0))
+    return int(r.value), int(h.value)

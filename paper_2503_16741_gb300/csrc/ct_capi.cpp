@@ -436,6 +436,63 @@ ct_status ct_back_acc(const ct_geometry *g, ct_projector proj, ct_mode mode, ct_
     return project(1, g, proj, mode, in_t, sino, out_t, vol, batch, alpha, beta, cuda_stream);
 }
 
+// Pooled workspace of one projection call, by the same rules the launchers
+// follow (k_sf.cu, k_nc_fwd.cu, k_nc_back.cu, k_ray.cu).
+static size_t workspace_rule(int dir, const ct_geometry *g, ct_projector proj, ct_mode mode, ct_dtype in_t,
+                             int batch) {
+    const CtGrid &G = g->grid;
+    const size_t vox = (size_t)g->nx * g->ny * g->nz * (size_t)batch;
+    const size_t cells = (size_t)g->nview * g->nv * g->nu * (size_t)batch;
+    const size_t isz = in_t == CT_F32 ? 4 : 2;
+    const bool nc = G.variant == ctp::GEO_NONCIRC_FLAT;
+    const bool zmajor = !G.is2d && g->nz % 4 == 0 && g->nz >= 8;  // the streaming forward's copy
+    if (mode == CT_MODE_RECON) return 0;
+    if (dir == 0) {
+        switch (proj) {
+        case CT_VOXEL: return !nc && zmajor ? vox * isz : 0;
+        case CT_RAY: return 0;
+        case CT_DD:
+            if (nc) return ctp::nc_footprint_fits(G, 1) ? vox * isz : 0;
+            return G.max_m_dd_u <= 3.5f && zmajor ? vox * isz : 0;
+        case CT_SF:
+            if (nc) return ctp::nc_footprint_fits(G, 0) ? vox * isz : 0;
+            return G.max_m_sf_u <= 3.5f && zmajor ? vox * isz : 0;
+        default:  // SF-TT: streaming forward in circular flat 3D geometry, footprint forward otherwise
+            return ctp::sftt_circ_fits(G) ? (zmajor ? vox * isz : 0) : vox * isz;
+        }
+    }
+    switch (proj) {
+    case CT_RAY: return nc ? 0 : cells * 4;
+    case CT_DD: return !nc || ctp::nc_footprint_fits(G, 1) ? cells * 4 : 0;
+    case CT_SF_TT: return cells * 4;
+    default: return 0;
+    }
+}
+
+ct_status ct_workspace_bytes(const ct_geometry *g, ct_projector proj, ct_mode mode, int direction, ct_dtype in_t,
+                             int batch, size_t *bytes) {
+    if (!g || !bytes) return fail(CT_ERR_INVALID_ARG, "null geometry or output pointer");
+    if (proj < CT_VOXEL || proj > CT_SF_TT) return fail(CT_ERR_INVALID_ARG, "unknown projector");
+    if (mode != CT_MODE_PROJ && mode != CT_MODE_RECON) return fail(CT_ERR_INVALID_ARG, "unknown mode");
+    if (direction != 0 && direction != 1) return fail(CT_ERR_INVALID_ARG, "direction must be 0 (forward) or 1 (back)");
+    if (in_t < CT_F32 || in_t > CT_BF16) return fail(CT_ERR_INVALID_ARG, "unknown dtype");
+    if (batch < 1) return fail(CT_ERR_INVALID_ARG, "batch must be >= 1");
+    *bytes = workspace_rule(direction, g, proj, mode, in_t, batch);
+    return CT_OK;
+}
+
+ct_status ct_workspace_limit(size_t bytes) {
+    const cudaError_t e = ctp::workspace_set_limit(bytes);
+    if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("workspace pool: ") + cudaGetErrorString(e));
+    return CT_OK;
+}
+
+ct_status ct_workspace_usage(size_t *reserved, size_t *used_high, int reset_high) {
+    const cudaError_t e = ctp::workspace_usage(reserved, used_high, reset_high);
+    if (e != cudaSuccess) return fail(CT_ERR_CUDA, std::string("workspace pool: ") + cudaGetErrorString(e));
+    return CT_OK;
+}
+
 ct_status ct_ramp_filter(const ct_geometry *g, ct_dtype in_t, const void *sino, ct_dtype out_t, void *out, int batch,
                          void *cuda_stream) {
     if (!g) return fail(CT_ERR_INVALID_ARG, "null geometry");

@@ -62,5 +62,10 @@ cudaError_t zmajor_copy(int elem_bytes, const void *x, void *xZ, int nx, int ny,
 // reach the driver's allocator).
 cudaError_t workspace_alloc(void **p, size_t bytes, cudaStream_t st);
 cudaError_t workspace_free(void *p, cudaStream_t st);
+// release threshold of the current device's pool (and a trim to it)
+cudaError_t workspace_set_limit(size_t bytes);
+// bytes the pool holds from the device now, and the high-water mark of the
+// bytes in use (reset to zero when reset_high is set)
+cudaError_t workspace_usage(size_t *reserved, size_t *used_high, int reset_high);
 
 }  // namespace ctp

@@ -41,7 +41,9 @@ def ls_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, steps: 
                         lr: Optional[float] = None, x0: Optional[torch.Tensor] = None,
                         stream=None, work: Optional[torch.Tensor] = None) -> torch.Tensor:
     """`steps` gradient steps on 1/2 ||A x - y||^2 from x0 (zeros by default).
-    y: (..., nview, [nv,] nu); returns x with y's batch shape and dtype."""
+    y: (..., nview, [nv,] nu); returns x with y's batch shape and dtype.  The
+    residual A x - y is kept in FP32 whatever y's storage type (in half
+    storage the difference of two close values would lose its digits)."""
     if lr is None:
         lr = ls_step_size(geom, projector)
     lead = y.shape[:-len(geom.sino_shape)]
@@ -49,7 +51,7 @@ def ls_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, steps: 
     with torch.cuda.stream(s):
         x = (torch.zeros(tuple(lead) + geom.vol_shape, dtype=y.dtype, device=y.device)
              if x0 is None else x0.clone())
-        r = torch.empty_like(y) if work is None else work
+        r = torch.empty(y.shape, dtype=torch.float32, device=y.device) if work is None else work
         for _ in range(steps):
             r.copy_(y)
             forward_acc(geom, x, r, 1.0, -1.0, projector, stream=s)
@@ -71,7 +73,8 @@ def os_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, n_subse
     """`epochs` passes over the ordered subsets, one gradient step on
     1/2 ||A_s x - y_s||^2 per subset s, with step lr[s] (default
     1 / ||A_s||^2 with the same 2 % margin as ls_step_size).
-    y: (..., nview, [nv,] nu); returns x with y's batch shape and dtype."""
+    y: (..., nview, [nv,] nu); returns x with y's batch shape and dtype
+    (residuals in FP32)."""
     subsets = subsets if subsets is not None else ordered_subsets(geom.nview, n_subsets)
     geoms = [geom.subset(v) for v in subsets]
     if lr is None:
@@ -82,7 +85,7 @@ def os_gradient_descent(geom: Geometry, y: torch.Tensor, projector: str, n_subse
     with torch.cuda.stream(s):
         idx = [torch.as_tensor(v, device=y.device) for v in subsets]
         ys = [y.index_select(y.dim() - k, i).contiguous() for i in idx]
-        rs = [torch.empty_like(t) for t in ys]
+        rs = [torch.empty(t.shape, dtype=torch.float32, device=t.device) for t in ys]
         x = (torch.zeros(tuple(lead) + geom.vol_shape, dtype=y.dtype, device=y.device)
              if x0 is None else x0.clone())
         for _ in range(epochs):

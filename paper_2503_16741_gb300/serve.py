@@ -9,7 +9,12 @@ free up and their work overlaps on the device.  Waiting requests with the
 same geometry, operation, projector and storage type are merged into one
 batched launch (the kernels treat batch items independently and
 deterministically, so each result is the same alone and in a batch).
-Geometry tables stay resident on the device between requests.
+Geometry tables stay resident on the device between requests, and a request
+may carry a device tensor and ask for its result on the device, so volumes
+and sinograms stay resident too.  Admission counts every byte a request
+holds on the device while it runs: its input, output and temporaries and the
+library's pooled workspace (ct_workspace_bytes), whose pool is capped at the
+budget.
 
 The scheduler is independent of the device: `Scheduler` drives an
 `Executor` (launch a group, poll it, collect results).  `GpuExecutor` runs
@@ -33,18 +38,21 @@ ITEMSIZE = {"f32": 4, "f16": 2, "bf16": 2}
 @dataclasses.dataclass(eq=False)
 class Request:
     """One job.  `geometry`: keyword arguments of `Geometry` (hashable once
-    frozen by `geometry_key`).  `data`: host array, the volume (fwd) or the
-    sinogram (back, mbir, fbp), shape (nz, ny, nx) / (nview, nv, nu) (2D:
-    without the z / v axis).  `dtype`: storage type on the device.  `fbp`
-    reconstructs by filtered backprojection (the projector is the recon
-    mode's voxel-driven one whatever `projector` says)."""
+    frozen by `geometry_key`).  `data`: the volume (fwd) or the sinogram
+    (back, mbir, fbp), shape (nz, ny, nx) / (nview, nv, nu) (2D: without the
+    z / v axis), as a host array or as a tensor already on the server's
+    device (used in place: no host copy).  `dtype`: storage type on the
+    device.  `out_device`: return the result as a device tensor instead of a
+    host array.  `fbp` reconstructs by filtered backprojection (the projector
+    is the recon mode's voxel-driven one whatever `projector` says)."""
     geometry: Dict[str, Any]
     op: str
-    data: np.ndarray
+    data: Any
     projector: str = "sf"
     dtype: str = "f32"
     iters: int = 10
     deadline_s: Optional[float] = None
+    out_device: bool = False
 
 
 def geometry_key(geom: Dict[str, Any]) -> Tuple:
@@ -64,12 +72,14 @@ def shapes(geom: Dict[str, Any]):
     return vol, sino
 
 
+def _on_device(data) -> bool:
+    return getattr(data, "is_cuda", False)
+
+
 def request_bytes(req: Request) -> int:
-    """Device bytes a request holds while it runs: input, output and, for
-    MBIR and FBP, the residual or filtered sinogram (FP32 for FBP).  The
-    library's own scratch (the z-major volume copy of the forwards, the
-    scaled FP32 sinogram of the DD, SF-TT and circular ray-driven backs)
-    comes from its stream-ordered pool and is not counted here."""
+    """Device bytes of a request's own buffers while it runs: input, output
+    and, for MBIR and FBP, the FP32 residual or filtered sinogram.  (The
+    GPU executor adds the library's pooled workspace.)"""
     vol, sino = shapes(req.geometry)
     nv, ns = int(np.prod(vol)), int(np.prod(sino))
     it = ITEMSIZE[req.dtype]
@@ -79,12 +89,12 @@ def request_bytes(req: Request) -> int:
         return (ns + nv) * it
     if req.op == "fbp":
         return (ns + nv) * it + ns * 4
-    return (2 * ns + nv) * it
+    return (ns + nv) * it + ns * 4
 
 
 def group_key(req: Request) -> Tuple:
     return (geometry_key(req.geometry), req.op, req.projector, req.dtype,
-            req.iters if req.op == "mbir" else 0)
+            req.iters if req.op == "mbir" else 0, _on_device(req.data), req.out_device)
 
 
 @dataclasses.dataclass(eq=False)
@@ -101,6 +111,10 @@ class Executor:
     request; release(handle) frees its device memory."""
 
     slots = 1
+
+    def request_bytes(self, req: Request) -> int:
+        """Device bytes the request holds while it runs (admission)."""
+        return request_bytes(req)
 
     def launch(self, slot: int, reqs: Sequence[Request]):  # pragma: no cover - interface
         raise NotImplementedError
@@ -137,6 +151,8 @@ class Scheduler:
         self.rejected = 0
         self.timed_out = 0
         self.launches = 0
+        self.memory_waits = 0  # admissions deferred because the budget was full while a slot was free
+        self._waiting_head = None
         self._stop = False
         self._thread = threading.Thread(target=self._run, name="ct-scheduler", daemon=True)
         self._thread.start()
@@ -147,7 +163,11 @@ class Scheduler:
         if req.op not in OPS:
             fut.set_exception(ValueError(f"unknown op {req.op!r}"))
             return fut
-        nbytes = request_bytes(req)
+        try:
+            nbytes = self.ex.request_bytes(req)
+        except Exception as e:  # noqa: BLE001 - a request the executor cannot size is rejected
+            fut.set_exception(e)
+            return fut
         with self._lock:
             if nbytes > self.budget:
                 self.rejected += 1
@@ -176,7 +196,8 @@ class Scheduler:
                     "timed_out": self.timed_out, "launches": self.launches,
                     "p50_ms": float(np.percentile(lat, 50) * 1e3),
                     "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                    "hbm_peak_bytes": self.peak_in_use, "queue_depth": len(self._queue)}
+                    "hbm_peak_bytes": self.peak_in_use, "queue_depth": len(self._queue),
+                    "memory_waits": self.memory_waits}
 
     # ---- scheduler thread
     def _take_group(self) -> Optional[List[_Pending]]:
@@ -188,6 +209,9 @@ class Scheduler:
             return None
         head = self._queue[0]
         if self.in_use + head.nbytes > self.budget:
+            if head is not self._waiting_head:  # count each deferred head once
+                self._waiting_head = head
+                self.memory_waits += 1
             return None
         key = group_key(head.req)
         group, total = [head], head.nbytes
@@ -312,6 +336,24 @@ class GpuExecutor(Executor):
         with self._plock:
             self._pinned[(tuple(buf.shape), buf.dtype)].append(buf)
 
+    def request_bytes(self, req: Request) -> int:
+        """The request's buffers plus the library workspace its calls take
+        (the larger of the forward's and the back's for MBIR: they run one
+        after the other on one stream, whose pool reuses the memory)."""
+        from .binding import workspace_bytes
+        g = self.geometry(req.geometry)
+        dt = self._dt[req.dtype]
+        if req.op == "fwd":
+            ws = workspace_bytes(g, req.projector, "fwd", dt)
+        elif req.op == "back":
+            ws = workspace_bytes(g, req.projector, "back", dt)
+        elif req.op == "mbir":
+            ws = max(workspace_bytes(g, req.projector, "fwd", dt),
+                     workspace_bytes(g, req.projector, "back", self.torch.float32))
+        else:
+            ws = workspace_bytes(g, "voxel", "back", self.torch.float32, mode="recon")
+        return request_bytes(req) + ws
+
     def geometry(self, g: Dict[str, Any]):
         key = geometry_key(g)
         if key not in self._geoms:
@@ -341,12 +383,20 @@ class GpuExecutor(Executor):
                 raise ValueError(f"input shape {r.data.shape} != {in_shape}")
         dt = self._dt[r0.dtype]
         stream = self.streams[slot]
-        host_in = self._pinned_buffer((len(reqs),) + tuple(in_shape), dt)
-        for k, r in enumerate(reqs):
-            host_in[k].copy_(torch.from_numpy(np.asarray(r.data, dtype=np.float32)))
+        resident = _on_device(r0.data)
+        host_in = None
+        if not resident:
+            host_in = self._pinned_buffer((len(reqs),) + tuple(in_shape), dt)
+            for k, r in enumerate(reqs):
+                host_in[k].copy_(torch.from_numpy(np.asarray(r.data, dtype=np.float32)))
         tmp = None  # a stream-ordered temporary that must outlive the launch
         with torch.cuda.stream(stream):
-            d_in = host_in.to(self.device, non_blocking=True)
+            if resident:  # device tensors: used in place (stacked when batched)
+                stream.wait_stream(torch.cuda.current_stream(self.device))
+                d_in = (r0.data.to(dt).reshape((1,) + tuple(in_shape)) if len(reqs) == 1 else
+                        torch.stack([r.data.to(dt) for r in reqs]))
+            else:
+                d_in = host_in.to(self.device, non_blocking=True)
             if r0.op == "fwd":
                 d_out = torch.empty((len(reqs),) + sino, dtype=dt, device=self.device)
                 forward_into(geom, d_in, d_out, r0.projector, stream=stream)
@@ -360,22 +410,29 @@ class GpuExecutor(Executor):
                 back_into(geom, tmp, d_out, "voxel", mode="recon", stream=stream)
             else:
                 d_out = ls_gradient_descent(geom, d_in, r0.projector, r0.iters, lr=lr, stream=stream)
-            host_out = self._pinned_buffer(tuple(d_out.shape), dt)
-            host_out.copy_(d_out, non_blocking=True)
+            host_out = None
+            if not r0.out_device:
+                host_out = self._pinned_buffer(tuple(d_out.shape), dt)
+                host_out.copy_(d_out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
         # keep device buffers alive until the event has passed
-        return {"event": ev, "host_out": host_out, "host_in": host_in, "keep": (d_in, d_out, tmp)}
+        return {"event": ev, "host_out": host_out, "host_in": host_in, "keep": (d_in, d_out, tmp),
+                "device_out": d_out if r0.out_device else None}
 
     def done(self, handle) -> bool:
         return handle["event"].query()
 
-    def results(self, handle) -> List[np.ndarray]:
+    def results(self, handle) -> List[Any]:
+        if handle.get("device_out") is not None:  # device-resident results (ready: the event passed)
+            d = handle["device_out"]
+            return [d[k] for k in range(d.shape[0])]
         out = handle["host_out"].float().numpy()
         return [out[k].copy() for k in range(out.shape[0])]
 
     def release(self, handle) -> None:
         handle["keep"] = None
+        handle["device_out"] = None
         for k in ("host_in", "host_out"):
             if handle.get(k) is not None:
                 self._return_pinned(handle[k])
@@ -388,7 +445,12 @@ class Server(Scheduler):
 
     def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 32 << 30,
                  max_batch: int = 8, executor: Optional[GpuExecutor] = None, **kw):
-        super().__init__(executor or GpuExecutor(device, slots), hbm_budget, max_batch=max_batch, **kw)
+        ex = executor or GpuExecutor(device, slots)
+        # the library's pool keeps no more freed workspace than the budget
+        from .binding import workspace_limit
+        ex.torch.cuda.set_device(ex.device)
+        workspace_limit(hbm_budget)
+        super().__init__(ex, hbm_budget, max_batch=max_batch, **kw)
 
 
 def poisson_arrivals(rate_hz: float, n: int, seed: int = 0) -> np.ndarray:
