@@ -127,6 +127,8 @@ class Geometry:
         unknown = set(params) - set(PER_VIEW)
         if unknown:
             raise TypeError(f"unknown geometry parameters {sorted(unknown)}")
+        if poses is None and ("sad" not in params or "sdd" not in params):
+            raise TypeError("sad and sdd are required (unless per-view poses are given)")
         self.kind, self.det = kind, det
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.nu, self.nv, self.nview = int(nu), int(nv), int(nview)
@@ -138,9 +140,13 @@ class Geometry:
         d.nu, d.nv, d.du, d.dv, d.nview = self.nu, self.nv, self.du, self.dv, self.nview
         self._keep = []
         self._params = {}  # per-view parameters as given (for subset())
-        for name in PER_VIEW:
-            val = params.get(name, 500.0 if name == "sad" else (1000.0 if name == "sdd" else 0.0))
-            arr = np.ascontiguousarray(np.atleast_1d(np.asarray(val, dtype=np.float64)).ravel())
+        for name in PER_VIEW:  # absent parameters are NULL: 0.0 for every view (sad, sdd: unused with poses)
+            if name not in params:
+                self._params[name] = np.zeros(1)
+                setattr(d, name, C.POINTER(C.c_double)())
+                setattr(d, "n_" + name, 0)
+                continue
+            arr = np.ascontiguousarray(np.atleast_1d(np.asarray(params[name], dtype=np.float64)).ravel())
             self._keep.append(arr)
             self._params[name] = arr
             setattr(d, name, arr.ctypes.data_as(C.POINTER(C.c_double)))

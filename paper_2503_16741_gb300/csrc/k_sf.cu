@@ -505,7 +505,7 @@ constexpr int kItems = 256;
 constexpr int kSlabSeg = 256;
 
 template <int RPT, int NA> struct SfFwdSmem {
-    float Z[8 * RPT][kItems];  // [row][item]: conflict-free in both stages
+    float Z[8 * RPT][kItems];  // [row][item]
     // the item's NA transaxial cell weights; rows padded by 8 so that lanes
     // reading one item's weights of different cells fall on different banks
     float Fu[NA][kItems + 8];
@@ -614,14 +614,16 @@ __device__ __forceinline__ void tt_stage1(const CtView &V, const CtGrid &g, cons
 // its upper edge once: the part below closes the row, whose sum is stored
 // once, and the rest opens the next.  d is the distance from the voxel's
 // lower edge to that row edge.  The walk runs over whole groups of four
-// voxels [k0 & ~3, k1 | 3] of the z-major column (nz a multiple of 4);
-// voxels outside [k0, k1] reach only rows outside the tile, whose sums are
-// dropped.  Rows the walk does not reach are zero.
+// voxels from k0 & ~3 (k0 & ~7 when nz is a multiple of 8) to k1 | 3 of the
+// z-major column (nz a multiple of 4); voxels outside [k0, k1] reach only
+// rows outside the tile, whose sums are dropped.  Rows the walk does not
+// reach are zero.
 template <typename TIn, bool DD, int BV>
 __device__ __forceinline__ void sf_sweep(const SfCol &C, const CtGrid &g, const CtView &V,
                                          const TIn *__restrict__ cz, int k0, int k1, int B0,
                                          float (&Z)[BV][kItems], int tid) {
-    const int ks = k0 & ~3, ke = k1 | 3;
+    // groups of eight from a sector boundary when nz is a multiple of 8
+    const int ks = (g.nz & 7) ? (k0 & ~3) : (k0 & ~7), ke = k1 | 3;
     const float w = C.sv;
     int bref;
     float frac;
@@ -722,24 +724,30 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
             // ---- stage 1: one item (column) per thread
             const int q = base + tid;
             if (q < total) {
-                int lo = 0, hi = nseg - 1;  // slab of item q: last t with off[t] <= q
+                // slab of item q: last t with off[t] <= q.  The warp searches
+                // for its first item (every lane reads the same offsets), then
+                // each lane steps forward to its own (a slab holds tens of items)
+                const int qw = base + (tid & ~31);
+                int lo = 0, hi = nseg - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (S.off[mid] <= q) lo = mid; else hi = mid - 1;
+                    if (S.off[mid] <= qw) lo = mid; else hi = mid - 1;
                 }
+                while (lo < nseg - 1 && S.off[lo + 1] <= q) ++lo;
                 const int s = seg + lo;
                 const int l = S.L0[lo] + (q - S.off[lo]);
                 const int i = main_y ? l : s, j = main_y ? s : l;
+                const int sl = tid;  // this item's slot in the shared arrays
                 if constexpr (VOX) {
-                    vx_stage1<TIn, CURVED, BV, NA>(V, g, i, j, B0, bt, x, volZ, S.Z, S.Fu, S.a0, tid);
+                    vx_stage1<TIn, CURVED, BV, NA>(V, g, i, j, B0, bt, x, volZ, S.Z, S.Fu, S.a0, sl);
                 } else {
                 const SfCol C = sf_col<CURVED, DD>(V, g, i, j);
                 int d0 = (int)floorf(C.T.k0 + 0.5f), d1 = (int)floorf(C.T.k3 + 0.5f);
                 float Fu[NA];
                 trap_cellsN<NA>(C.T, d0, d1, Fu);
 #pragma unroll
-                for (int r = 0; r < NA; ++r) S.Fu[r][tid] = Fu[r];
-                S.a0[tid] = C.aref + d0;
+                for (int r = 0; r < NA; ++r) S.Fu[r][sl] = Fu[r];
+                S.a0[sl] = C.aref + d0;
                 // voxels whose axial rectangle can meet a row of the tile
                 const float hw = 0.5f + (TT ? V.m_tt_v : C.hv) + kSearchPad;
                 const float rsv = 1.f / C.sv;
@@ -751,12 +759,12 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                     // axial rectangle shorter than a row, column contiguous in
                     // the z-major copy (nz a multiple of 4): one sweep down z
                     const TIn *cz = volZ + (size_t)bt * g.nx * g.ny * g.nz + ((size_t)j * g.nx + i) * g.nz;
-                    sf_sweep<TIn, DD, BV>(C, g, V, cz, k0, k1, B0, S.Z, tid);
+                    sf_sweep<TIn, DD, BV>(C, g, V, cz, k0, k1, B0, S.Z, sl);
                 } else {
 #pragma unroll
-                for (int r = 0; r < BV; ++r) S.Z[r][tid] = 0.f;
+                for (int r = 0; r < BV; ++r) S.Z[r][sl] = 0.f;
                 if constexpr (TT) {
-                    tt_stage1<TIn, BV>(V, g, C, i, j, B0, bt, x, volZ, S.Z, tid);
+                    tt_stage1<TIn, BV>(V, g, C, i, j, B0, bt, x, volZ, S.Z, sl);
                 } else {
                 const TIn *xc = x + (size_t)j * g.nx + i;
                 const size_t zs = (size_t)g.nx * g.ny;
@@ -773,8 +781,8 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         float Fv0, Fv1;
                         two_rows(vf - C.hv, vf + C.hv, e0, Fv0, Fv1);
                         const int r0 = bref + e0 - B0;
-                        if (r0 >= 0 && r0 < BV) S.Z[r0][tid] = fmaf(Fv0, val, S.Z[r0][tid]);
-                        if (r0 + 1 >= 0 && r0 + 1 < BV) S.Z[r0 + 1][tid] = fmaf(Fv1, val, S.Z[r0 + 1][tid]);
+                        if (r0 >= 0 && r0 < BV) S.Z[r0][sl] = fmaf(Fv0, val, S.Z[r0][sl]);
+                        if (r0 + 1 >= 0 && r0 + 1 < BV) S.Z[r0 + 1][sl] = fmaf(Fv1, val, S.Z[r0 + 1][sl]);
                     }
                 } else {
                     for (int k = k0; k <= k1; ++k) {
@@ -787,7 +795,7 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         for (int e = e0; e <= e1; ++e) {
                             const int r = bref + e - B0;
                             if (r >= 0 && r < BV)
-                                S.Z[r][tid] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[r][tid]);
+                                S.Z[r][sl] = fmaf(overlap(vf - C.hv, vf + C.hv, e - 0.5f, e + 0.5f), val, S.Z[r][sl]);
                         }
                     }
                 }
@@ -815,11 +823,12 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                     for (int c = c0; c <= c1; ++c) {
                         const int item = S.off[t] + c - base;
                         if (item < 0 || item >= kItems) continue;
-                        const int d = a - S.a0[item];
+                        const int sl = item;
+                        const int d = a - S.a0[sl];
                         if (d < 0 || d >= NA) continue;
-                        const float w = S.Fu[d][item];
+                        const float w = S.Fu[d][sl];
 #pragma unroll
-                        for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[threadIdx.y + 8 * r][item], acc[r]);
+                        for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[threadIdx.y + 8 * r][sl], acc[r]);
                     }
                 }
             }

@@ -87,3 +87,13 @@ def test_calls_on_a_null_geometry_are_rejected(lib):
     assert lib.ct_back(None, 3, 0, 0, None, 0, None, 1, None) == 1
     lib.ct_geometry_destroy.argtypes = [C.c_void_p]
     assert lib.ct_geometry_destroy(None) == 0
+
+
+def test_geometry_requires_sad_and_sdd(lib):
+    """The header's rule (sad and sdd must be given) holds in the binding too:
+    no silent default distances."""
+    from paper_2503_16741_gb300.binding import Geometry
+    with pytest.raises(TypeError, match="sad and sdd"):
+        Geometry("circ3d", "flat", 8, 8, 8, 1.0, 1.0, 1.0, 16, 8, 1.0, 1.0, 4, theta=0.0)
+    with pytest.raises(TypeError, match="sad and sdd"):
+        Geometry("circ3d", "flat", 8, 8, 8, 1.0, 1.0, 1.0, 16, 8, 1.0, 1.0, 4, sad=500.0)

@@ -97,3 +97,20 @@ def test_mbir_gradient_descent_reduces_the_data_term(ct):
         losses.append(float(loss.detach()))
     assert all(b < a for a, b in zip(losses, losses[1:])), losses
     assert losses[-1] < 0.5 * losses[0], losses
+
+
+def test_projector_module_recon_mode(ct):
+    """Projector(mode='recon', direction='backward') is the FBP
+    backprojection of filtered projections (ct_back in CT_MODE_RECON)."""
+    from paper_2503_16741_gb300.autograd import Projector
+    spec = W.scaled(W.circ3d_256(), 32, 40)
+    g = ct.Geometry.from_spec(spec)
+    y = torch.rand(g.sino_shape, device="cuda")
+    q = ct.ramp_filter(g, y)
+    for method in ("voxel", "DD", "SF"):
+        got = Projector(g, "recon", method, "backward")(q)
+        ref = ct.back(g, q, method.lower(), mode="recon")
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+    with pytest.raises(ValueError):
+        Projector(g, "recon", "SF", "forward")
