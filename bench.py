@@ -291,6 +291,57 @@ def serving_bench(dev_index: int, n_req: int, dtype: str, budget: int, loads=(0.
             "error_vs_fp64": errs, "max_rel_l2_vs_fp64": max((e["rel_l2_vs_fp64"] for e in errs), default=None)}
 
 
+def serving_budget_bound(dev_index: int, n_req: int = 200, budget: int = 512 << 20):
+    """FP32 against FP16 storage under an admission budget that binds: the
+    same requests (those of the serving mix whose FP32 size fits the budget),
+    device-resident, closed loop; served requests per second, the times a
+    ready request waited for memory, and the peak admitted bytes."""
+    import torch
+
+    from paper_2503_16741_gb300.serve import GpuExecutor, Request, Server
+    dev = torch.device("cuda", dev_index)
+    ex = GpuExecutor(dev_index, slots=4)
+    picked = []
+    for f, u in serving_mix(8 * n_req, seed=3):
+        probe = Request(f["geometry"], f["op"], None, projector=f["projector"], dtype="f32", iters=f["iters"])
+        if ex.request_bytes(probe) <= budget:
+            picked.append((f, u))
+        if len(picked) == n_req:
+            break
+    for f, _ in picked:
+        if f["op"] == "mbir":
+            ex.step_size(f["geometry"], f["projector"])
+    out = {"hbm_budget_bytes": budget, "requests": len(picked)}
+    for dtype, T in (("f32", torch.float32), ("f16", torch.float16)):
+        gen = torch.Generator(device=dev).manual_seed(1)
+        reqs = []
+        for f, _ in picked:
+            spec = f["spec"]
+            vol = (spec.ny, spec.nx) if spec.kind == "fan2d" else spec.vol_shape
+            sino = (spec.nview, spec.nu) if spec.kind == "fan2d" else spec.sino_shape
+            data = torch.rand(vol if f["op"] == "fwd" else sino, generator=gen, device=dev).to(T)
+            reqs.append(Request(f["geometry"], f["op"], data, projector=f["projector"], dtype=dtype,
+                                iters=f["iters"], out_device=True))
+        srv = Server(hbm_budget=budget, max_batch=4, executor=ex)
+        for fut in [srv.submit(r) for r in reqs[:8]]:
+            fut.result(timeout=600)
+        srv.close()
+        srv = Server(hbm_budget=budget, max_batch=4, executor=ex)
+        t0 = time.perf_counter()
+        futs = [srv.submit(r) for r in reqs]
+        for fut in futs:
+            fut.result(timeout=600)
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        out[dtype] = {"served_req_per_s": len(reqs) / dt, "served_gupdates_per_s": sum(u for _, u in picked) / dt / 1e9,
+                      "memory_waits": st["memory_waits"], "hbm_peak_bytes": st["hbm_peak_bytes"],
+                      "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"]}
+        del reqs, futs
+    out["f16_over_f32"] = out["f16"]["served_req_per_s"] / out["f32"]["served_req_per_s"]
+    return out
+
+
 def run_suite(args):
     """Forward and back time of every projector on each workload (one JSON
     line per case): GUpdates/s per direction at the storage types given."""
@@ -707,6 +758,7 @@ def main():
         loads = tuple(float(v) for v in args.serve_loads.split(","))
         out["serving"] = [serving_bench(local, args.serve_requests, "f32", budget, loads),
                           serving_bench(local, args.serve_requests, "f16", budget, loads)]
+        out["serving_budget_bound"] = serving_budget_bound(local)
         out["serving_mix"] = (serving_mix.__doc__.split("Returns")[0].strip().replace("\n    ", " ")
                               + " Inputs and results device-resident; open-loop Poisson arrivals at "
                               f"{args.serve_loads} of the measured closed-loop saturation (top-level figures at "
