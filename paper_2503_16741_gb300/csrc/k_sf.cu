@@ -347,7 +347,14 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                     nc_cells<4>(C.T, d0, d1, F);  // antiderivative at the interior cell edges only
                 else
                     trap_cells4(C.T, d0, d1, F);
-                const int as = window4(F, C.aref + d0, g.nu, Fu);
+                int as;
+                if (C.aref + d0 <= g.nu - 4) {  // the 4-cell window starts at the footprint
+                    as = C.aref + d0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) Fu[q] = F[q];
+                } else {
+                    as = window4(F, C.aref + d0, g.nu, Fu);
+                }
                 // Rows relative to the chunk's first voxel: voxel kk sits at
                 // rel = frac0 + sv kk rows from row bref0 (0 < sv < 1), so it
                 // touches rows e0, e0 + 1 with e0 in [-1, ZT - 1].
@@ -359,8 +366,23 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                 const int va = max(ef, -bref0), vb = min(el, g.nv - 1 - bref0);  // rows on the detector
                 const TIn *ya = yv + as;
                 for (int e = ef; e < min(va, el + 1); ++e) Rs[e + 1][tid] = 0.f;  // a chunk below the detector zeroes [ef, el] only
-#pragma unroll 4
-                for (int e = va; e <= vb; ++e) {
+                // two rows per step in packed FP32x2 arithmetic (each lane
+                // rounds as the scalar form would)
+                float2 Fu2[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Fu2[q] = make_float2(Fu[q], Fu[q]);
+                int e = va;
+#pragma unroll 2
+                for (; e < vb; e += 2) {
+                    const TIn *r0 = ya + (size_t)(bref0 + e) * g.nu, *r1 = r0 + g.nu;
+                    float2 R = __fmul2_rn(Fu2[0], make_float2(ld(r0, 0), ld(r1, 0)));
+                    R = __ffma2_rn(Fu2[1], make_float2(ld(r0, 1), ld(r1, 1)), R);
+                    R = __ffma2_rn(Fu2[2], make_float2(ld(r0, 2), ld(r1, 2)), R);
+                    R = __ffma2_rn(Fu2[3], make_float2(ld(r0, 3), ld(r1, 3)), R);
+                    Rs[e + 1][tid] = R.x;
+                    Rs[e + 2][tid] = R.y;
+                }
+                if (e == vb) {
                     const TIn *row = ya + (size_t)(bref0 + e) * g.nu;
                     float R = Fu[0] * ld(row, 0);
                     R = fmaf(Fu[1], ld(row, 1), R);
@@ -378,17 +400,38 @@ sf_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                 const int e0 = lo0 < -0.5f ? -1 : 0;  // == ef
                 float d = ((float)e0 + 0.5f) - lo0;
                 const float *rp = &Rs[e0 + 1][tid];
-                float wz = fmaf((float)kbeg, g.dz, V.o[2]);
+                const float wz0 = fmaf((float)kbeg, g.dz, V.o[2]);
+                auto step = [&]() {  // the current voxel's row integral; advances the sweep
+                    const bool cross = d < w;
+                    const float f0 = cross ? d : w;
+                    const float sum = fmaf(f0, rp[0], (w - f0) * rp[128]);
+                    rp += cross ? 128 : 0;
+                    d = (cross ? d + 1.f : d) - w;
+                    return sum;
+                };
+                // voxels in pairs: amplitudes and accumulation in packed FP32x2
 #pragma unroll
-                for (int kk = 0; kk < ZT; ++kk) {
-                    if (kbeg + kk < kend) {
-                        const bool cross = d < w;
-                        const float f0 = cross ? d : w;
-                        const float sum = fmaf(f0, rp[0], (w - f0) * rp[128]);
-                        acc[kk] = fmaf(RECON ? rw : fp_amp<DD>(C, wz), sum, acc[kk]);
-                        rp += cross ? 128 : 0;
-                        d = (cross ? d + 1.f : d) - w;
-                        wz += g.dz;
+                for (int kk = 0; kk < ZT; kk += 2) {
+                    if (kbeg + kk + 1 < kend) {
+                        const float s0 = step(), s1 = step();
+                        float2 amp;
+                        if (RECON) {
+                            amp = make_float2(rw, rw);
+                        } else if (DD) {
+                            amp = make_float2(1.f, 1.f);
+                        } else {
+                            const float2 wz2 = make_float2(fmaf((float)kk, g.dz, wz0), fmaf((float)(kk + 1), g.dz, wz0));
+                            const float2 t = __ffma2_rn(wz2, wz2, make_float2(C.rxy2, C.rxy2));
+                            amp = __fmul2_rn(__fmul2_rn(make_float2(C.invm, C.invm), t),
+                                             make_float2(rsqrtf(t.x), rsqrtf(t.y)));
+                        }
+                        const float2 a2 = __ffma2_rn(amp, make_float2(s0, s1), make_float2(acc[kk], acc[kk + 1]));
+                        acc[kk] = a2.x;
+                        acc[kk + 1] = a2.y;
+                    } else if (kbeg + kk < kend) {
+                        const float s0 = step();
+                        const float wz = fmaf((float)kk, g.dz, wz0);
+                        acc[kk] = fmaf(RECON ? rw : fp_amp<DD>(C, wz), s0, acc[kk]);
                     }
                 }
                 continue;
