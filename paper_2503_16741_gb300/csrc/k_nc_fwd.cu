@@ -114,11 +114,12 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
     const bool lines = isfinite(ln1.c0) && isfinite(ln1.ck) && isfinite(ln1.cs) && isfinite(ln2.c0) &&
                        isfinite(ln2.ck) && isfinite(ln2.cs);
     const bool live = a < g.nu && rb < g.nv;
-    float acc[4][4];
+    // sums of rows rb + r, cells (a, a + 1) and (a + 2, a + 3): packed FP32x2
+    float2 acc[4][2];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+        for (int c = 0; c < 2; ++c) acc[r][c] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int s = 0; s < nslab; ++s) {
         const float fs = (float)s;
@@ -187,12 +188,13 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
                             const int q = d + c;
                             wu[c] = (q >= 0 && q < NA) ? S.Fu[q][idx] : 0.f;
                         }
+                        const float2 w01 = make_float2(wu[0], wu[1]), w23 = make_float2(wu[2], wu[3]);
+                        const float fr[4] = {fv.x, fv.y, fv.z, fv.w};
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            acc[0][c] = fmaf(wu[c], fv.x, acc[0][c]);
-                            acc[1][c] = fmaf(wu[c], fv.y, acc[1][c]);
-                            acc[2][c] = fmaf(wu[c], fv.z, acc[2][c]);
-                            acc[3][c] = fmaf(wu[c], fv.w, acc[3][c]);
+                        for (int r = 0; r < 4; ++r) {
+                            const float2 f = make_float2(fr[r], fr[r]);
+                            acc[r][0] = __ffma2_rn(w01, f, acc[r][0]);
+                            acc[r][1] = __ffma2_rn(w23, f, acc[r][1]);
                         }
                     }
                 }
@@ -207,9 +209,11 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int ac = a + c;
+            const float2 p = acc[r][c >> 1];
+            const float sum = (c & 1) ? p.y : p.x;
             if (ac < g.nu)
                 st_out(g, sino, (((size_t)bt * g.nview + v) * g.nv + b) * g.nu + ac,
-                       KIND != NC_SF ? acc[r][c] * nc_cell_factor<KIND>(V, g, ac, b) : acc[r][c], out_t);
+                       KIND != NC_SF ? sum * nc_cell_factor<KIND>(V, g, ac, b) : sum, out_t);
         }
     }
 }
