@@ -118,16 +118,41 @@ vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__
                 const float r = fmaf(w1, ld(row, (size_t)ac1), w0 * ld(row, (size_t)ac0));
                 Rs[e][tid] = (b >= 0 && b < g.nv) ? r : 0.f;
             }
+            // voxels in pairs, in packed FP32x2 arithmetic (each lane rounds
+            // as the scalar form would)
 #pragma unroll
-            for (int kk = 0; kk < ZT; ++kk) {
+            for (int kk = 0; kk < ZT; kk += 2) {
                 const int k = kbeg + kk;
-                if (k >= kend) break;
-                const float fv = fmaf(C.sv, (float)k, C.fv0);
-                const float bf = floorf(fv);
-                const float tb = fv - bf;
-                const int e0 = min(max((int)bf - B, 0), NR - 2);
-                const float sb = fmaf(tb, Rs[e0 + 1][tid], (1.f - tb) * Rs[e0][tid]);
-                acc[kk] = fmaf(RECON ? wr : vx_amp_col(C, g, V, k), sb, acc[kk]);
+                if (k + 1 < kend) {
+                    const float2 fv = __ffma2_rn(make_float2(C.sv, C.sv), make_float2((float)k, (float)(k + 1)),
+                                                 make_float2(C.fv0, C.fv0));
+                    const float2 bf = make_float2(floorf(fv.x), floorf(fv.y));
+                    const float2 tb = __fadd2_rn(fv, make_float2(-bf.x, -bf.y));
+                    const int e0 = min(max((int)bf.x - B, 0), NR - 2), e1 = min(max((int)bf.y - B, 0), NR - 2);
+                    const float2 sb = __ffma2_rn(tb, make_float2(Rs[e0 + 1][tid], Rs[e1 + 1][tid]),
+                                                 __fmul2_rn(__fadd2_rn(make_float2(1.f, 1.f), make_float2(-tb.x, -tb.y)),
+                                                            make_float2(Rs[e0][tid], Rs[e1][tid])));
+                    float2 amp;
+                    if (RECON) {
+                        amp = make_float2(wr, wr);
+                    } else {
+                        const float2 wz = __ffma2_rn(make_float2((float)k, (float)(k + 1)), make_float2(g.dz, g.dz),
+                                                     make_float2(V.o[2], V.o[2]));
+                        const float2 t = __ffma2_rn(wz, wz, make_float2(C.rxy2, C.rxy2));
+                        amp = __fmul2_rn(make_float2(C.amp1, C.amp1),
+                                         __fmul2_rn(t, make_float2(rsqrtf(t.x), rsqrtf(t.y))));
+                    }
+                    const float2 a2 = __ffma2_rn(amp, sb, make_float2(acc[kk], acc[kk + 1]));
+                    acc[kk] = a2.x;
+                    acc[kk + 1] = a2.y;
+                } else if (k < kend) {
+                    const float fv = fmaf(C.sv, (float)k, C.fv0);
+                    const float bf = floorf(fv);
+                    const float tb = fv - bf;
+                    const int e0 = min(max((int)bf - B, 0), NR - 2);
+                    const float sb = fmaf(tb, Rs[e0 + 1][tid], (1.f - tb) * Rs[e0][tid]);
+                    acc[kk] = fmaf(RECON ? wr : vx_amp_col(C, g, V, k), sb, acc[kk]);
+                }
             }
             continue;
         }
