@@ -41,6 +41,34 @@ __device__ __forceinline__ void ld4(const __nv_bfloat16 *__restrict__ p, float v
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// eight consecutive elements from an address aligned to 8 elements (one
+// 32-byte sector of FP32, one 16-byte load of FP16 / BF16)
+__device__ __forceinline__ void ld8(const float *__restrict__ p, float v[8]) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(__cvta_generic_to_global(p)));
+}
+__device__ __forceinline__ void ld8(const __half *__restrict__ p, float v[8]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+    const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[t]));
+        v[2 * t] = f.x;
+        v[2 * t + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void ld8(const __nv_bfloat16 *__restrict__ p, float v[8]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
+    const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[t]));
+        v[2 * t] = f.x;
+        v[2 * t + 1] = f.y;
+    }
+}
+
 // out_t: 0 = f32, 1 = f16, 2 = bf16; one rounding at the store
 __device__ __forceinline__ void st(void *out, size_t i, float v, int out_t) {
     if (out_t == 0)

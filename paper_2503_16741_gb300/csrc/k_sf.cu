@@ -689,9 +689,16 @@ __device__ __forceinline__ void sf_sweep(const SfCol &C, const CtGrid &g, const 
         r += cross ? 1 : 0;
         d = (cross ? d + 1.f : d) - w;
     };
-    // eight voxels (one 32-byte sector of FP32) per iteration: both halves
-    // of the sector are requested together
+    // eight voxels (one 32-byte sector of FP32) per iteration
     int kq = ks;
+    if ((g.nz & 7) == 0) {  // groups start on 8-element boundaries: one vector load each
+        for (; kq + 7 <= ke; kq += 8) {
+            float x8[8];
+            ld8(cz + kq, x8);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) step(x8[t]);
+        }
+    }
     for (; kq + 7 <= ke; kq += 8) {
         float xa[4], xb[4];
         ld4(cz + kq, xa);
