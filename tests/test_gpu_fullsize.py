@@ -103,3 +103,21 @@ def test_noncirc_512_full_size_dd(ct):
     xb = ct.back(g, y, "dd")
     ref = oracle.back_voxels(spec, "dd", y.double().cpu().numpy(), sel)
     assert rel_l2(xb.cpu().numpy().ravel()[sel], ref) <= TOL_F32
+
+
+@pytest.mark.parametrize("workload,proj", [("circ3d_256", "sf"), ("circ3d_256", "dd"), ("noncirc3d_saddle", "sf")])
+def test_full_size_adjoint_identity(ct, workload, proj):
+    """<A x, y> = <x, A^T y> at the benchmark sizes, on the code paths the
+    benchmark times (the forward's axial sweep with vector column loads, the
+    back's packed row filter; the footprint kernels in non-circular
+    geometry), with the dot products taken in FP64."""
+    spec = getattr(W, workload)()
+    g = ct.Geometry.from_spec(spec)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.rand(g.vol_shape, generator=gen, device="cuda")
+    y = torch.rand(g.sino_shape, generator=gen, device="cuda")
+    ax = ct.forward(g, x, proj)
+    aty = ct.back(g, y, proj)
+    lhs = float((ax.double() * y.double()).sum())
+    rhs = float((x.double() * aty.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
