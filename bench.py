@@ -57,8 +57,8 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # prefix of the kernel's .cu at capture time (the bench reports null once the
 # source differs).
 NCU = {
-    "sf_fwd": {"dram_bytes": 927.1e6, "l2_bytes": 30.487e9, "l2_peak_gbs": 36405.0, "src": "3a7822078bd301a7"},
-    "sf_back": {"dram_bytes": 353.9e6, "l2_bytes": 23.023e9, "l2_peak_gbs": 36403.0, "src": "3a7822078bd301a7"},
+    "sf_fwd": {"dram_bytes": 918.6e6, "l2_bytes": 30.464e9, "l2_peak_gbs": 36408.0, "src": "49e2ad73bd92b8d6"},
+    "sf_back": {"dram_bytes": 355.1e6, "l2_bytes": 23.008e9, "l2_peak_gbs": 36405.0, "src": "49e2ad73bd92b8d6"},
 }
 
 
