@@ -677,10 +677,16 @@ __device__ __forceinline__ void sf_sweep(const SfCol &C, const CtGrid &g, const 
     float d = ((float)e0 + 0.5f) - lo;  // to that row's upper edge: (0, 1]
     const int rfirst = r;
     float acc = 0.f;
-    float wz = fmaf((float)ks, g.dz, V.o[2]);
-    auto step = [&](float x) {
-        const float val = fp_amp<DD>(C, wz) * x;
-        wz += g.dz;
+    const float wz0 = fmaf((float)ks, g.dz, V.o[2]);
+    // amplitude x value of voxels ks + t, ks + t + 1, in packed FP32x2
+    auto vals = [&](int t, float x0, float x1) {
+        if (DD) return make_float2(x0, x1);
+        const float2 wz2 = make_float2(fmaf((float)t, g.dz, wz0), fmaf((float)(t + 1), g.dz, wz0));
+        const float2 q = __ffma2_rn(wz2, wz2, make_float2(C.rxy2, C.rxy2));
+        const float2 amp = __fmul2_rn(__fmul2_rn(make_float2(C.invm, C.invm), q), make_float2(rsqrtf(q.x), rsqrtf(q.y)));
+        return __fmul2_rn(amp, make_float2(x0, x1));
+    };
+    auto step = [&](float val) {
         const bool cross = d < w;
         const float sum = fmaf(cross ? d : w, val, acc);
         const float rest = (w - d) * val;
@@ -696,23 +702,33 @@ __device__ __forceinline__ void sf_sweep(const SfCol &C, const CtGrid &g, const 
             float x8[8];
             ld8(cz + kq, x8);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) step(x8[t]);
+            for (int t = 0; t < 8; t += 2) {
+                const float2 v2 = vals(kq - ks + t, x8[t], x8[t + 1]);
+                step(v2.x);
+                step(v2.y);
+            }
         }
     }
     for (; kq + 7 <= ke; kq += 8) {
-        float xa[4], xb[4];
-        ld4(cz + kq, xa);
-        ld4(cz + kq + 4, xb);
+        float x8[8];
+        ld4(cz + kq, x8);
+        ld4(cz + kq + 4, x8 + 4);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) step(xa[t]);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) step(xb[t]);
+        for (int t = 0; t < 8; t += 2) {
+            const float2 v2 = vals(kq - ks + t, x8[t], x8[t + 1]);
+            step(v2.x);
+            step(v2.y);
+        }
     }
     if (kq <= ke) {
         float xa[4];
         ld4(cz + kq, xa);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) step(xa[t]);
+        for (int t = 0; t < 4; t += 2) {
+            const float2 v2 = vals(kq - ks + t, xa[t], xa[t + 1]);
+            step(v2.x);
+            step(v2.y);
+        }
     }
     if ((unsigned)r < (unsigned)BV) Z[r][tid] = acc;
     for (int q = 0; q < min(rfirst, BV); ++q) Z[q][tid] = 0.f;
@@ -877,8 +893,20 @@ sf_fwd_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ 
                         const int d = a - S.a0[sl];
                         if (d < 0 || d >= NA) continue;
                         const float w = S.Fu[d][sl];
+                        if constexpr (RPT % 2 == 0) {  // row pairs in packed FP32x2
+                            const float2 w2 = make_float2(w, w);
 #pragma unroll
-                        for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[threadIdx.y + 8 * r][sl], acc[r]);
+                            for (int r = 0; r < RPT; r += 2) {
+                                const float2 p = __ffma2_rn(
+                                    w2, make_float2(S.Z[threadIdx.y + 8 * r][sl], S.Z[threadIdx.y + 8 * r + 8][sl]),
+                                    make_float2(acc[r], acc[r + 1]));
+                                acc[r] = p.x;
+                                acc[r + 1] = p.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) acc[r] = fmaf(w, S.Z[threadIdx.y + 8 * r][sl], acc[r]);
+                        }
                     }
                 }
             }
