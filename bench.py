@@ -57,8 +57,8 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # prefix of the kernel's .cu at capture time (the bench reports null once the
 # source differs).
 NCU = {
-    "sf_fwd": {"dram_bytes": 918.6e6, "l2_bytes": 30.464e9, "l2_peak_gbs": 36408.0, "src": "49e2ad73bd92b8d6"},
-    "sf_back": {"dram_bytes": 355.1e6, "l2_bytes": 23.008e9, "l2_peak_gbs": 36405.0, "src": "49e2ad73bd92b8d6"},
+    "sf_fwd": {"dram_bytes": 935.3e6, "l2_bytes": 30.472e9, "l2_peak_gbs": 36275.0, "src": "27b5509270244406"},
+    "sf_back": {"dram_bytes": 353.1e6, "l2_bytes": 23.183e9, "l2_peak_gbs": 36275.0, "src": "27b5509270244406"},
 }
 
 
