@@ -149,13 +149,18 @@ __device__ __forceinline__ void nc_fp(const CtView &V, const CtGrid &g, int i, i
         const float f1 = vr + V.Kv * __fdividef(fmaf(-rv, hzn, hzv), cn + hzn);
         const float f2 = vr + V.Kv * __fdividef(fmaf(rv, hzn, -hzv), cn - hzn);
         const float vlo = fminf(f1, f2), vhi = fmaxf(f1, f2);
-        const int e0 = (int)floorf(vlo + 0.5f);
+        // overlaps with rows e0 .. e0 + NB - 1 (row e covers [e - 1/2, e + 1/2]);
+        // vlo lies below the first row's upper edge m, so each later row's
+        // overlap starts at its lower edge (equal to overlap() bit for bit)
+        const float ef = floorf(vlo + 0.5f);
+        float m = ef + 0.5f;
+        P.Fv[0] = fmaxf(fminf(vhi, m) - fmaxf(vlo, m - 1.f), 0.f);
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const float e = (float)(e0 + q);
-            P.Fv[q] = overlap(vlo, vhi, e - 0.5f, e + 0.5f);
+        for (int q = 1; q < NB; ++q) {
+            P.Fv[q] = fmaxf(fminf(vhi, m + 1.f) - m, 0.f);
+            m += 1.f;
         }
-        P.b0 = bref + e0;
+        P.b0 = bref + (int)ef;
         P.size = 0.5f * ((T.k3 - T.k0) + (T.k2 - T.k1)) * (vhi - vlo);
     }
     P.cn = cn;

@@ -57,30 +57,47 @@ nc_back(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino
                 const TIn *yv = ys + (size_t)(v0 + vv) * vstride;
                 NcFp<NA, NB> P;
                 nc_fp<KIND, NA, NB>(V, g, i, j, k, P);
-                // cells off the detector get weight 0 and a clamped (in-bounds)
-                // address; cells past the footprint are not read
-                int ac[NA];
-                float wu[NA];
-#pragma unroll
-                for (int c = 0; c < NA; ++c) {
-                    const int ca = P.a0 + c;
-                    const bool in = ca >= 0 && ca < g.nu;
-                    ac[c] = in ? ca : 0;
-                    wu[c] = in ? P.Fu[c] : 0.f;
-                }
                 float s = 0.f;
+                if (P.a0 >= 0 && P.a0 + NA <= g.nu) {
+                    // the whole window on the detector: one row pointer and
+                    // predicated loads of the footprint's cells (no branches)
 #pragma unroll
-                for (int q = 0; q < NB; ++q) {
-                    const int b = P.b0 + q;
-                    if (P.Fv[q] != 0.f && b >= 0 && b < g.nv) {
-                        const TIn *row = yv + (size_t)b * g.nu;
-                        float rs = wu[0] * ld(row, (size_t)ac[0]);
+                    for (int q = 0; q < NB; ++q) {
+                        const int b = P.b0 + q;
+                        if (P.Fv[q] != 0.f && b >= 0 && b < g.nv) {
+                            const TIn *row = yv + (size_t)b * g.nu + P.a0;
+                            float rs = P.Fu[0] * ld(row, 0);
 #pragma unroll
-                        for (int c = 1; c < NA; ++c) {
-                            if (c >= P.n) break;
-                            rs = fmaf(wu[c], ld(row, (size_t)ac[c]), rs);
+                            for (int c = 1; c < NA; ++c)
+                                rs = fmaf(P.Fu[c], c < P.n ? ld(row, (size_t)c) : 0.f, rs);
+                            s = fmaf(P.Fv[q], rs, s);
                         }
-                        s = fmaf(P.Fv[q], rs, s);
+                    }
+                } else {
+                    // cells off the detector get weight 0 and a clamped
+                    // (in-bounds) address; cells past the footprint are not read
+                    int ac[NA];
+                    float wu[NA];
+#pragma unroll
+                    for (int c = 0; c < NA; ++c) {
+                        const int ca = P.a0 + c;
+                        const bool in = ca >= 0 && ca < g.nu;
+                        ac[c] = in ? ca : 0;
+                        wu[c] = in ? P.Fu[c] : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) {
+                        const int b = P.b0 + q;
+                        if (P.Fv[q] != 0.f && b >= 0 && b < g.nv) {
+                            const TIn *row = yv + (size_t)b * g.nu;
+                            float rs = wu[0] * ld(row, (size_t)ac[0]);
+#pragma unroll
+                            for (int c = 1; c < NA; ++c) {
+                                if (c >= P.n) break;
+                                rs = fmaf(wu[c], ld(row, (size_t)ac[c]), rs);
+                            }
+                            s = fmaf(P.Fv[q], rs, s);
+                        }
                     }
                 }
                 a = fmaf(RECON ? V.rc_w / (P.cn * P.cn * P.size) : P.amp, s, a);
