@@ -225,6 +225,13 @@ ct_status ct_geometry_create(const ct_geometry_desc *d, ct_geometry **out) {
             rows[r][2] = (float)(h[2] * axes[r].z);
             rows[r][3] = (float)dot(o, axes[r]);
         }
+        {
+            const float hxu = 0.5f * V.au[0], hyu = 0.5f * V.au[1], hxn = 0.5f * V.an[0], hyn = 0.5f * V.an[1];
+            V.cdu[0] = -hxu - hyu; V.cdu[1] = hxu - hyu; V.cdu[2] = hyu - hxu; V.cdu[3] = hxu + hyu;
+            V.cdn[0] = -hxn - hyn; V.cdn[1] = hxn - hyn; V.cdn[2] = hyn - hxn; V.cdn[3] = hxn + hyn;
+            V.hzv = 0.5f * V.av[2];
+            V.hzn = 0.5f * V.an[2];
+        }
         V.o[0] = (float)o.x; V.o[1] = (float)o.y; V.o[2] = (float)o.z;
         V.eu[0] = (float)eu.x; V.eu[1] = (float)eu.y; V.eu[2] = (float)eu.z;
         V.ev[0] = (float)ev.x; V.ev[1] = (float)ev.y; V.ev[2] = (float)ev.z;

@@ -34,9 +34,14 @@ struct alignas(16) CtView {
     float rc_R;       // recon mode: R = (O - s).n, the source's distance to the rotation centre O
     float rc_c;       // recon mode: step (h0 + 2 sum_{odd k < nu} h_k), the ramp's response to a constant row
     float m_tt_v;     // bound on the SF-TT axial knots' distance from fv(centre), rows
-    float pad[3];
+    // offsets of a voxel's four transaxial corners from its centre (corners
+    // (-,-), (+,-), (-,+), (+,+) in (x, y)) along e_u and along n, and half
+    // its height along e_v and n (mm; single precision, as the kernels use them)
+    float cdu[4], cdn[4];
+    float hzv, hzn;
+    float pad;
 };
-static_assert(sizeof(CtView) == 44 * 4, "CtView layout");
+static_assert(sizeof(CtView) == 52 * 4, "CtView layout");
 
 enum GeoVariant { GEO_CIRC_FLAT = 0, GEO_CIRC_CURVED = 1, GEO_NONCIRC_FLAT = 2 };
 

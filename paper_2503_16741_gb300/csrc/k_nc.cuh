@@ -59,11 +59,12 @@ __device__ __forceinline__ int nc_cells(const Trap &T, int d0, int d1, float (&F
 #pragma unroll
     for (int q = 0; q < N; ++q) F[q] = 0.f;
     const int nlast = d1 - d0;  // index of the last cell
+    const float e0 = (float)d0 + 0.5f;  // right edge of the first cell (exact)
     float Gp = 0.f;
 #pragma unroll
     for (int q = 0; q < N - 1; ++q) {
         if (q >= nlast) break;
-        const float Gn = trap_G(T, (float)(d0 + q) + 0.5f);
+        const float Gn = trap_G(T, e0 + (float)q);
         F[q] = Gn - Gp;
         Gp = Gn;
     }
@@ -109,19 +110,17 @@ __device__ __forceinline__ void nc_fp(const CtView &V, const CtGrid &g, int i, i
         const float lo = fminf(e1, e2), hi = fmaxf(e1, e2);
         T = nc_trap(lo, lo, hi, hi);
     } else {  // the four transaxial corners, sorted into a trapezoid
-        const float hxu = 0.5f * V.au[0], hxn = 0.5f * V.an[0];
-        const float hyu = 0.5f * V.au[1], hyn = 0.5f * V.an[1];
-        float t0 = fr + V.Ku * __fdividef(fmaf(-r, -hxn - hyn, -hxu - hyu), cn - hxn - hyn);
-        float t1 = fr + V.Ku * __fdividef(fmaf(-r, hxn - hyn, hxu - hyu), cn + hxn - hyn);
-        float t2 = fr + V.Ku * __fdividef(fmaf(-r, hyn - hxn, hyu - hxu), cn - hxn + hyn);
-        float t3 = fr + V.Ku * __fdividef(fmaf(-r, hxn + hyn, hxu + hyu), cn + hxn + hyn);
+        float t0 = fr + V.Ku * __fdividef(fmaf(-r, V.cdn[0], V.cdu[0]), cn + V.cdn[0]);
+        float t1 = fr + V.Ku * __fdividef(fmaf(-r, V.cdn[1], V.cdu[1]), cn + V.cdn[1]);
+        float t2 = fr + V.Ku * __fdividef(fmaf(-r, V.cdn[2], V.cdu[2]), cn + V.cdn[2]);
+        float t3 = fr + V.Ku * __fdividef(fmaf(-r, V.cdn[3], V.cdu[3]), cn + V.cdn[3]);
         sort4(t0, t1, t2, t3);
         T = nc_trap(t0, t1, t2, t3);
     }
     const int d0 = (int)floorf(T.k0 + 0.5f), d1 = (int)floorf(T.k3 + 0.5f);
     P.n = nc_cells<NA>(T, d0, d1, P.Fu);
     P.a0 = aref + d0;
-    const float hzv = 0.5f * V.av[2], hzn = 0.5f * V.an[2];
+    const float hzv = V.hzv, hzn = V.hzn;
     if (KIND == NC_TT) {
         if (g.is2d) {  // one row of unit height, inside the axial plateau: factor 1
 #pragma unroll
