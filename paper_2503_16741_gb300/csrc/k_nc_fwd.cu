@@ -74,6 +74,7 @@ __device__ __forceinline__ NcLine nc_line(const CtView &V, const SlabCoef &c, fl
 }
 
 constexpr int kNcMaxV = 1024;  // voxels cached per round
+constexpr int kNcViewBlock = 32;  // views of one tile adjacent in the grid
 
 template <int NA> struct NcCache {
     float4 Fv[2][kNcMaxV];  // rows 4 g0 .. 4 g0 + 7 of the tile
@@ -90,11 +91,17 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     NcCache<NA> &S = *reinterpret_cast<NcCache<NA> *>(smem_raw);
     __shared__ NcBox tile;  // the CTA's box coefficients (read as broadcasts)
+    // CTA order: kNcViewBlock consecutive views of one tile, then tiles, then
+    // view blocks.  Neighbouring views of a tile read nearly the same voxels,
+    // so CTAs resident together share their slabs in L2.
     int bx = blockIdx.x;
+    const int vl = bx % kNcViewBlock; bx /= kNcViewBlock;
     const int tu = bx % tiles_u; bx /= tiles_u;
     const int tv = bx % tiles_v; bx /= tiles_v;
-    const int v = bx % g.nview;
-    const int bt = bx / g.nview;
+    const int nvb = (g.nview + kNcViewBlock - 1) / kNcViewBlock;
+    const int v = (bx % nvb) * kNcViewBlock + vl;
+    const int bt = bx / nvb;
+    if (v >= g.nview) return;  // the last block's missing views (whole CTA)
     const int tid = threadIdx.y * 16 + threadIdx.x;
     const int A0 = tu * 64, B0 = tv * 64;
     const int a = A0 + 4 * threadIdx.x, ty = threadIdx.y, rb = B0 + 4 * ty;
@@ -239,7 +246,8 @@ template <typename TIn, int KIND, int NA, int NB> struct NcFwd {
             return e;
         }
         const int tiles_u = (g.nu + 63) / 64, tiles_v = (g.nv + 63) / 64;
-        dim3 blk(16, 16), grd((unsigned)((size_t)tiles_u * tiles_v * g.nview * batch));
+        const size_t nvb = (g.nview + kNcViewBlock - 1) / kNcViewBlock;
+        dim3 blk(16, 16), grd((unsigned)((size_t)kNcViewBlock * tiles_u * tiles_v * nvb * batch));
         nc_fwd<TIn, KIND, NA, NB><<<grd, blk, smem, st>>>(g, views, src, xZ, out, out_t, tiles_u, tiles_v);
         e = cudaGetLastError();
         if (xZ) {
