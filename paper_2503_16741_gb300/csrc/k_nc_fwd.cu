@@ -182,19 +182,20 @@ nc_fwd(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ vol, 
                         lo = max(la, (int)ceilf(fminf(u1, u2) - 1e-3f));
                         hi = min(lb, (int)floorf(fmaxf(u1, u2) + 1e-3f));
                     }
-                    for (int l = lo; l <= hi; ++l) {
-                        const int idx = (l - lc) * nkr + (k - kc);
+                    int idx = (lo - lc) * nkr + (k - kc);
+                    for (int l = lo; l <= hi; ++l, idx += nkr) {
                         const int2 ag = S.ag[idx];
                         const int d = a - ag.x;  // first cell of the thread in the footprint
                         const int gd = ty - ag.y;
-                        if ((unsigned)gd > 1u || d <= -4 || d >= NA) continue;
+                        if ((unsigned)gd > 1u || (unsigned)(d + 3) >= (unsigned)(NA + 3)) continue;  // -4 < d < NA
                         const float4 fv = S.Fv[gd][idx];
+                        // Fu[d + c][idx] for the thread's cells c: one base offset
+                        const float *fu = &S.Fu[0][0];
+                        const int off = d * kNcMaxV + idx;
                         float wu[4];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int q = d + c;
-                            wu[c] = (q >= 0 && q < NA) ? S.Fu[q][idx] : 0.f;
-                        }
+                        for (int c = 0; c < 4; ++c)
+                            wu[c] = (unsigned)(d + c) < (unsigned)NA ? fu[off + c * kNcMaxV] : 0.f;
                         const float2 w01 = make_float2(wu[0], wu[1]), w23 = make_float2(wu[2], wu[3]);
                         const float fr[4] = {fv.x, fv.y, fv.z, fv.w};
 #pragma unroll
