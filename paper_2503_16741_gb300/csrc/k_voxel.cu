@@ -72,7 +72,7 @@ __device__ __forceinline__ float bilinear(const TIn *yv, const CtGrid &g, float 
 // rows (the same operations, in the same order, as the per-voxel bilinear);
 // chunks whose rows do not fit the slice take the per-voxel form.
 template <typename TIn, bool CURVED, int ZT, bool RECON = false>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 vx_back_circ(CtGrid g, const CtView *__restrict__ views, const TIn *__restrict__ sino,
              void *__restrict__ vol, int out_t, int tiles_x, int nzc) {
     constexpr int NR = ZT + 1;  // rows floor(fv) - B .. + 1 of the chunk's voxels, B the first voxel's row
