@@ -2,7 +2,10 @@
 
 * all-pairs brute force (slab method per ray and voxel, no traversal);
 * closed-form chords through the volume box and through grid-aligned blocks;
-* convergence of a voxelised disk to the analytic chord 2 mu sqrt(r^2 - d^2).
+* convergence of a voxelised disk to the analytic chord 2 mu sqrt(r^2 - d^2);
+* first-order convergence of a voxelised ellipse (fan beam), ball (circular
+  cone beam) and rotated ellipsoid (tilted non-circular pose) to the chord
+  of the ray line through the quadric.
 """
 import math
 
@@ -114,3 +117,103 @@ def test_disk_converges_to_analytic_chord():
         errs.append(np.linalg.norm(y - want) / np.linalg.norm(want))
     assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:])), errs
     assert errs[-1] < 0.01
+
+
+def _quadric_chord(s, d, c, Q):
+    """Length of the line s + t d inside the quadric (X - c)^T Q (X - c) <= 1:
+    with alpha = d^T Q d, beta = d^T Q (s - c), gamma = (s - c)^T Q (s - c),
+    the roots of alpha t^2 + 2 beta t + gamma - 1 = 0 are 2 sqrt(beta^2 -
+    alpha (gamma - 1)) / alpha apart in t, i.e. that times |d| in mm."""
+    w = s - c
+    alpha, beta, gamma = d @ Q @ d, d @ Q @ w, w @ Q @ w
+    disc = beta * beta - alpha * (gamma - 1.0)
+    return 2.0 * math.sqrt(disc) / alpha * np.linalg.norm(d) if disc > 0 else 0.0
+
+
+def _rotation(a, b, c):
+    """Rotation matrix from z-y-x angles (radians)."""
+    ca, sa, cb, sb, cc, sc = math.cos(a), math.sin(a), math.cos(b), math.sin(b), math.cos(c), math.sin(c)
+    Rz = np.array([[ca, -sa, 0], [sa, ca, 0], [0, 0, 1]])
+    Ry = np.array([[cb, 0, sb], [0, 1, 0], [-sb, 0, cb]])
+    Rx = np.array([[1, 0, 0], [0, cc, -sc], [0, sc, cc]])
+    return Rz @ Ry @ Rx
+
+
+def _converges(errs, final, rate=None):
+    """Errors fall with every refinement, below `final` at the finest grid;
+    with `rate`, each halving of the voxel divides the error by at least
+    that factor (a voxelised boundary converges at first order in h)."""
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:])), errs
+    if rate is not None:
+        assert all(e0 / e1 > rate for e0, e1 in zip(errs, errs[1:])), errs
+    assert errs[-1] < final, errs
+
+
+def test_ellipse_converges_to_analytic_chord():
+    """Uniform ellipse (semi-axes 22 and 12 mm, rotated 0.6 rad, centred at
+    (6, -4) mm, mu = 0.02): the ray-driven projection of the voxelised
+    ellipse tends to mu times the line's chord through the ellipse."""
+    mu, fov = 0.02, 64.0
+    c = np.array([6.0, -4.0, 0.0])
+    R = _rotation(0.6, 0.0, 0.0)
+    Q = R @ np.diag([1 / 22.0 ** 2, 1 / 12.0 ** 2, 0.0]) @ R.T
+    errs = []
+    for n in (32, 64, 128, 256):
+        h = fov / n
+        spec = W.GeometrySpec("fan2d", "flat", n, n, 1, h, h, 1.0, 101, 1, 0.7, 1.0, 1,
+                              theta=1.1, sad=400.0, sdd=800.0)
+        g = (np.arange(n) - (n - 1) / 2) * h
+        X, Y = np.meshgrid(g, g)
+        P = np.stack([X - c[0], Y - c[1], np.zeros_like(X)], axis=-1)
+        img = np.where(np.einsum("...i,ij,...j->...", P, Q, P) <= 1.0, mu, 0.0)[None]
+        y = oracle.forward(spec, "ray", img)[0, 0]
+        s = oracle.frame(spec, 0)["s"]
+        want = np.array([mu * _quadric_chord(s, oracle.cell_point(spec, 0, a, 0) - s, c, Q) for a in range(101)])
+        assert (want > 0).sum() > 30
+        errs.append(np.linalg.norm(y - want) / np.linalg.norm(want))
+    _converges(errs, 0.01, rate=1.6)
+
+
+def _solid_3d(kind, quadric, c, mu, n, fov, nu, nv, du, **kw):
+    h = fov / n
+    spec = W.GeometrySpec(kind, "flat", n, n, n, h, h, h, nu, nv, du, du, 1, sad=300.0, sdd=600.0, **kw)
+    g = (np.arange(n) - (n - 1) / 2) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    P = np.stack([X - c[0], Y - c[1], Z - c[2]], axis=-1)
+    img = np.where(np.einsum("...i,ij,...j->...", P, quadric, P) <= 1.0, mu, 0.0)
+    y = oracle.forward(spec, "ray", img)[0]
+    s = oracle.frame(spec, 0)["s"]
+    want = np.array([[mu * _quadric_chord(s, oracle.cell_point(spec, 0, a, b) - s, c, quadric)
+                      for a in range(nu)] for b in range(nv)])
+    return y, want
+
+
+def test_ball_converges_to_analytic_chord_3d():
+    """Uniform ball (radius 18 mm at (5, -3, 4) mm, mu = 0.02) in circular cone
+    beam: the projection of the voxelised ball tends to 2 mu sqrt(r^2 - d^2),
+    d the distance from the ball's centre to the ray."""
+    r, mu = 18.0, 0.02
+    c = np.array([5.0, -3.0, 4.0])
+    errs = []
+    for n in (16, 32, 64, 128):
+        y, want = _solid_3d("circ3d", np.eye(3) / r ** 2, c, mu, n, 64.0, 27, 21, 3.0, theta=0.5)
+        assert (want > 0).sum() > 150
+        errs.append(np.linalg.norm(y - want) / np.linalg.norm(want))
+    _converges(errs, 0.025, rate=1.6)
+
+
+def test_ellipsoid_converges_to_analytic_chord_noncircular():
+    """Uniform ellipsoid (semi-axes 20, 14, 10 mm, rotated, off centre) seen
+    from a tilted, rolled non-circular pose: the projection of the voxelised
+    ellipsoid tends to mu times the line's chord through the ellipsoid."""
+    mu = 0.02
+    c = np.array([-4.0, 3.0, -2.0])
+    R = _rotation(0.4, -0.7, 0.3)
+    Q = R @ np.diag([1 / 20.0 ** 2, 1 / 14.0 ** 2, 1 / 10.0 ** 2]) @ R.T
+    errs = []
+    for n in (16, 32, 64, 128):
+        y, want = _solid_3d("noncirc3d", Q, c, mu, n, 64.0, 27, 21, 3.0, theta=2.2, phi=0.15, psi=0.1,
+                            z_src=3.0, u_ofst=1.5, v_ofst=-2.0)
+        assert (want > 0).sum() > 100
+        errs.append(np.linalg.norm(y - want) / np.linalg.norm(want))
+    _converges(errs, 0.025, rate=1.6)
