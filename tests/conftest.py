@@ -14,3 +14,25 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (run with -m gpu)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+_MEASURED = []
+
+
+@pytest.fixture
+def report(request):
+    """Records a measured figure of the test (an error against the oracle, a
+    convergence sequence): printed with the test and repeated in the
+    terminal summary, so a quiet run (-q) still shows it."""
+    def _report(line: str) -> None:
+        text = f"{request.node.name}: {line}"
+        print(text)
+        _MEASURED.append(text)
+    return _report
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    if _MEASURED:
+        terminalreporter.section("measured figures")
+        for line in _MEASURED:
+            terminalreporter.write_line(line)

@@ -39,7 +39,7 @@ def ct():
 @pytest.mark.parametrize("tin,tout,bound", CASES)
 @pytest.mark.parametrize("proj", PROJECTORS)
 @pytest.mark.parametrize("kind", ["circ3d", "noncirc3d"])
-def test_half_storage_forward_and_back(ct, kind, proj, tin, tout, bound):
+def test_half_storage_forward_and_back(ct, report, kind, proj, tin, tout, bound):
     assert bound <= TOL_F16 or "bf16" in (tin, tout)
     spec = ragged(kind, "flat", seed=7)
     g = ct.Geometry.from_spec(spec)
@@ -51,7 +51,7 @@ def test_half_storage_forward_and_back(ct, kind, proj, tin, tout, bound):
     x_ref = oracle.back(spec, proj, s)
     xb = ct.back(g, torch.as_tensor(s, dtype=T[tin]).cuda(), proj, out_dtype=T[tout])
     e_back = rel_l2(xb.float().cpu().numpy(), x_ref)
-    print(f"{kind} {proj} {tin}->{tout}: forward {e_fwd:.2e}, back {e_back:.2e}")
+    report(f"{kind} {proj} {tin}->{tout}: forward {e_fwd:.2e}, back {e_back:.2e}")
     assert e_fwd <= bound and e_back <= bound, (e_fwd, e_back)
 
 

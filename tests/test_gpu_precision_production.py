@@ -76,7 +76,7 @@ PARAMS = [(n, p, tin, tout, b) for n in GEOMS for p in _projectors(n) for (tin, 
 
 @pytest.mark.parametrize("name,proj,tin,tout,bound", PARAMS,
                          ids=[f"{n}-{p}-{i}-{o}" for n, p, i, o, _ in PARAMS])
-def test_half_storage_on_production_paths(ct, name, proj, tin, tout, bound):
+def test_half_storage_on_production_paths(ct, report, name, proj, tin, tout, bound):
     assert bound <= TOL_F16 or "bf16" in (tin, tout)
     spec = _spec(name)
     x, s = _inputs(name)
@@ -87,7 +87,7 @@ def test_half_storage_on_production_paths(ct, name, proj, tin, tout, bound):
     torch.cuda.synchronize()
     e_fwd = rel_l2(y.float().cpu().numpy(), y_ref)
     e_back = rel_l2(xb.float().cpu().numpy(), x_ref)
-    print(f"{name} {proj} {tin}->{tout}: forward {e_fwd:.2e}, back {e_back:.2e} (bound {bound:.2e})")
+    report(f"{name} {proj} {tin}->{tout}: forward {e_fwd:.2e}, back {e_back:.2e} (bound {bound:.2e})")
     assert e_fwd <= bound and e_back <= bound, (e_fwd, e_back)
 
 
@@ -99,7 +99,7 @@ def _sample_voxels(spec, n, seed):
 @pytest.mark.parametrize("proj", ["sf", "dd"])
 @pytest.mark.parametrize("tin,tout,bound", [("f16", "f16", 2.0 ** -10 + ARITH),
                                             ("bf16", "bf16", 2.0 ** -7 + ARITH)])
-def test_circ3d_256_full_size_half_storage(ct, proj, tin, tout, bound):
+def test_circ3d_256_full_size_half_storage(ct, report, proj, tin, tout, bound):
     """The 256^3 / 360-view workload at full size in half storage: the
     forward on four views and the back at 300 sampled voxels, both against
     the FP64 oracle on the unrounded inputs."""
@@ -115,5 +115,5 @@ def test_circ3d_256_full_size_half_storage(ct, proj, tin, tout, bound):
     torch.cuda.synchronize()
     sel = _sample_voxels(spec, 300, 6)
     e_back = rel_l2(xb.float().cpu().numpy().ravel()[sel], oracle.back_voxels(spec, proj, s, sel))
-    print(f"circ3d_256 full size {proj} {tin}->{tout}: forward {e_fwd:.2e}, back {e_back:.2e}")
+    report(f"circ3d_256 full size {proj} {tin}->{tout}: forward {e_fwd:.2e}, back {e_back:.2e}")
     assert e_fwd <= bound and e_back <= bound, (e_fwd, e_back)
