@@ -187,3 +187,19 @@ def test_footprint_mass_and_detector_roll(proj, psi, report):
     ratio = oracle.forward(spec, proj, x)[0].sum() / _cell_average(spec, c, Q).sum() / vol
     report(f"mass ratio {ratio:.6f}, cos^2 psi {math.cos(psi) ** 2:.6f}")
     assert abs(ratio - math.cos(psi) ** 2) < 2e-4, (ratio, math.cos(psi) ** 2)
+
+
+@pytest.mark.parametrize("psi", [0.0, 0.1, 0.3])
+def test_voxel_driven_mass_is_exact_under_roll(psi, report):
+    """The voxel-driven projection spreads each voxel's exact projected mass
+    (R8's amplitude) over bilinear weights that sum to one, so its total
+    equals the voxelised ball's exact cell-integrated projection at any
+    roll; the cos^2 psi of the footprint methods is theirs alone."""
+    r = 8.0
+    c, Q = np.zeros(3), np.eye(3) / r ** 2
+    spec = _spec("noncirc3d", 64, theta=2.2, psi=psi)
+    x = _voxelise(spec, c, Q)
+    vol = x.sum() / MU * spec.dx ** 3 / (4.0 / 3.0 * math.pi * r ** 3)
+    ratio = oracle.forward(spec, "voxel", x)[0].sum() / _cell_average(spec, c, Q).sum() / vol
+    report(f"mass ratio {ratio:.7f}")
+    assert abs(ratio - 1.0) < 2e-5, ratio
